@@ -1,0 +1,519 @@
+// extern "C" entry points (include/rchfsi.h): argument checks, host/device staging and the
+// outer loop of Algorithm 1.  Every C++ exception is turned into a status code here.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "solver.cuh"
+
+using namespace rchfsi;
+
+namespace rchfsi {
+void resid_form_f64(cudaStream_t s, int64_t m, int64_t n, const double* AX, const double* BX, const double* lam,
+                    double* W);
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guarded(rchfsi_ctx* h, F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    if (h) h->err = e.what();
+    g_last_error = e.what();
+    if (h && h->s) {
+      cudaStreamSynchronize(h->s);
+      cudaGetLastError();
+    }
+    return e.code;
+  } catch (const std::exception& e) {
+    if (h) h->err = e.what();
+    g_last_error = e.what();
+    return RCHFSI_ERR_CUDA;
+  }
+}
+
+void validate_params(const rchfsi_params* p) {
+  RC_CHECK(p, RCHFSI_ERR_INVALID_ARG, "params is NULL");
+  RC_CHECK(p->m > 0, RCHFSI_ERR_INVALID_ARG, "m must be positive");
+  RC_CHECK(p->block >= 1 && p->block <= p->m, RCHFSI_ERR_INVALID_ARG, "block must be in [1, m]");
+  RC_CHECK(p->nev >= 1 && p->nev <= p->block, RCHFSI_ERR_INVALID_ARG, "nev must be in [1, block]");
+  RC_CHECK(p->degree >= 1 && p->degree <= 4096, RCHFSI_ERR_INVALID_ARG, "degree must be in [1, 4096]");
+  RC_CHECK(p->precision >= RCHFSI_FP64 && p->precision <= RCHFSI_BF16, RCHFSI_ERR_INVALID_ARG, "bad precision");
+  RC_CHECK(p->method == RCHFSI_METHOD_RCHFSI || p->method == RCHFSI_METHOD_CHFSI, RCHFSI_ERR_INVALID_ARG,
+           "bad method");
+  RC_CHECK(p->field == RCHFSI_REAL || p->field == RCHFSI_COMPLEX, RCHFSI_ERR_INVALID_ARG, "bad field");
+  RC_CHECK(p->field == RCHFSI_REAL, RCHFSI_ERR_UNSUPPORTED, "complex Hermitian problems are not implemented");
+  RC_CHECK(p->max_iter >= 0 && p->min_iter >= 0, RCHFSI_ERR_INVALID_ARG, "iteration counts must be >= 0");
+  RC_CHECK(p->lanczos_steps >= 2 && p->lanczos_steps <= p->m, RCHFSI_ERR_INVALID_ARG,
+           "lanczos_steps must be in [2, m]");
+  RC_CHECK(p->tol >= 0.0, RCHFSI_ERR_INVALID_ARG, "tol must be >= 0");
+  RC_CHECK(p->block <= 6144, RCHFSI_ERR_UNSUPPORTED, "block larger than 6144");
+}
+
+void need_op(rchfsi_ctx* h) {
+  RC_CHECK(h, RCHFSI_ERR_INVALID_ARG, "handle is NULL");
+  RC_CHECK(h->has_op, RCHFSI_ERR_NO_OPERATOR, "rchfsi_set_operator has not been called");
+}
+
+// Copy n doubles (host or device) to a device buffer.
+void to_device(rchfsi_ctx& c, const double* src, double* dst, size_t n) {
+  RC_CHECK(src, RCHFSI_ERR_INVALID_ARG, "NULL input array");
+  const auto kind = is_device_pointer(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  RC_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, c.s));
+}
+
+void from_device(rchfsi_ctx& c, const double* src, double* dst, size_t n) {
+  if (!dst) return;
+  const auto kind = is_device_pointer(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  RC_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, c.s));
+}
+
+// Row-major m x N caller block -> column-major device block.
+void load_block(rchfsi_ctx& c, const double* src, double* dst_col) {
+  RC_CHECK(src, RCHFSI_ERR_INVALID_ARG, "NULL block argument");
+  const int64_t m = c.p.m;
+  const int N = c.p.block;
+  const double* d = src;
+  if (!is_device_pointer(src)) {
+    double* st = c.w.stage_in.ensure((size_t)m * N);
+    RC_CUDA(cudaMemcpyAsync(st, src, sizeof(double) * m * N, cudaMemcpyHostToDevice, c.s));
+    d = st;
+  }
+  transpose_f64(c.s, m, N, d, N, dst_col, m);
+}
+
+// Column-major device block -> row-major m x N caller block.
+void store_block(rchfsi_ctx& c, const double* src_col, double* dst) {
+  if (!dst) return;
+  const int64_t m = c.p.m;
+  const int N = c.p.block;
+  if (is_device_pointer(dst)) {
+    transpose_f64(c.s, N, m, src_col, m, dst, N);
+  } else {
+    double* st = c.w.stage_out.ensure((size_t)m * N);
+    transpose_f64(c.s, N, m, src_col, m, st, N);
+    RC_CUDA(cudaMemcpyAsync(dst, st, sizeof(double) * m * N, cudaMemcpyDeviceToHost, c.s));
+  }
+}
+
+std::vector<double> host_vec(rchfsi_ctx& c, const double* src, size_t n) {
+  RC_CHECK(src, RCHFSI_ERR_INVALID_ARG, "NULL vector argument");
+  std::vector<double> v(n);
+  const auto kind = is_device_pointer(src) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  RC_CUDA(cudaMemcpyAsync(v.data(), src, n * sizeof(double), kind, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  return v;
+}
+
+void set_dense(rchfsi_ctx& c, const rchfsi_operator* op) {
+  const int64_t m = c.p.m;
+  const size_t mm = (size_t)m * m;
+  DenseOp& d = c.dense;
+  RC_CHECK(op->A, RCHFSI_ERR_INVALID_ARG, "dense operator needs A");
+  RC_CHECK(!(op->Dinv && op->Dinv_dense), RCHFSI_ERR_INVALID_ARG, "give Dinv or Dinv_dense, not both");
+  d.AD32.release(); d.DA32.release(); d.ADtf.release(); d.DAtf.release(); d.AD16.release(); d.DA16.release();
+  to_device(c, op->A, d.A.ensure(mm), mm);
+  d.has_B = op->B != nullptr;
+  if (d.has_B) to_device(c, op->B, d.B.ensure(mm), mm);
+  else d.B.release();
+  d.has_dinv = op->Dinv != nullptr;
+  d.has_dinv_dense = op->Dinv_dense != nullptr;
+  if (d.has_dinv) to_device(c, op->Dinv, d.Dinv.ensure(m), m);
+  else d.Dinv.release();
+  if (d.has_dinv_dense) to_device(c, op->Dinv_dense, d.Dinv_dense.ensure(mm), mm);
+  else d.Dinv_dense.release();
+  // F = the matrix used inside the filter
+  const double* F = d.A.p;
+  DevBuf<double> fbuf;
+  if (op->A_filter) {
+    to_device(c, op->A_filter, fbuf.ensure(mm), mm);
+    F = fbuf.p;
+  }
+  double* AD = d.AD64.ensure(mm);
+  double* DA = d.DA64.ensure(mm);
+  if (d.has_dinv) {
+    scale_rows_f64(c.s, m, m, F, AD, d.Dinv.p, true);   // A~ D^-1: column scaling
+    scale_rows_f64(c.s, m, m, F, DA, d.Dinv.p, false);  // D^-1 A~: row scaling
+  } else if (d.has_dinv_dense) {
+    DevBuf<double> tmp;
+    tmp.ensure(mm);
+    EpiArgs e;
+    e.kind = EPI_STORE;
+    e.C = tmp.p;
+    e.ldc = m;
+    gemm_f64(c.s, m, m, m, F, m, true, d.Dinv_dense.p, m, false, e);  // col-major (F D)
+    transpose_f64(c.s, m, m, tmp.p, m, AD, m);
+    gemm_f64(c.s, m, m, m, d.Dinv_dense.p, m, true, F, m, false, e);  // col-major (D F)
+    transpose_f64(c.s, m, m, tmp.p, m, DA, m);
+    RC_CUDA(cudaStreamSynchronize(c.s));
+  } else {
+    RC_CUDA(cudaMemcpyAsync(AD, F, mm * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(DA, F, mm * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+  }
+  RC_CUDA(cudaStreamSynchronize(c.s));
+}
+
+void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
+  RC_CHECK(op->n_cells > 0 && op->n_c > 0 && op->n_c <= 128, RCHFSI_ERR_INVALID_ARG,
+           "FE operator needs n_cells > 0 and 0 < n_c <= 128");
+  RC_CHECK(op->cell_dofs && op->A_cells && op->B_cells && op->Dinv, RCHFSI_ERR_INVALID_ARG,
+           "FE operator needs cell_dofs, A_cells, B_cells and Dinv");
+  RC_CHECK(!op->A_filter && !op->Dinv_dense, RCHFSI_ERR_UNSUPPORTED,
+           "A_filter / Dinv_dense are for dense operators");
+  c.fe.reset(new FeOp());
+  FeOp& f = *c.fe;
+  f.m = c.p.m;
+  f.n_cells = op->n_cells;
+  f.nc = op->n_c;
+  f.B_shared = op->B_cells_shared != 0;
+  const size_t nd = (size_t)f.n_cells * f.nc;
+  const size_t na = nd * f.nc;
+  int* dofs = f.dofs.ensure(nd);
+  const auto kind = is_device_pointer(op->cell_dofs) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  RC_CUDA(cudaMemcpyAsync(dofs, op->cell_dofs, nd * sizeof(int), kind, c.s));
+  // validate the connectivity on the host before any kernel indexes with it
+  std::vector<int> hd(nd);
+  RC_CUDA(cudaMemcpyAsync(hd.data(), dofs, nd * sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  for (size_t i = 0; i < nd; ++i)
+    RC_CHECK(hd[i] >= 0 && hd[i] < c.p.m, RCHFSI_ERR_INVALID_ARG, "cell_dofs entry out of [0, m)");
+  to_device(c, op->A_cells, f.A64.ensure(na), na);
+  const size_t nb = f.B_shared ? (size_t)f.nc * f.nc : na;
+  to_device(c, op->B_cells, f.B64.ensure(nb), nb);
+  to_device(c, op->Dinv, f.Dinv.ensure(c.p.m), c.p.m);
+  RC_CUDA(cudaStreamSynchronize(c.s));
+}
+
+}  // namespace
+
+namespace rchfsi {
+// W = AX - BX diag(lam), column-major
+namespace {
+__global__ void resid_form_kernel(int64_t m, int64_t n, const double* AX, const double* BX, const double* lam,
+                                  double* W) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int64_t j = e / m;
+    W[e] = AX[e] - BX[e] * lam[j];
+  }
+}
+}  // namespace
+void resid_form_f64(cudaStream_t s, int64_t m, int64_t n, const double* AX, const double* BX, const double* lam,
+                    double* W) {
+  int64_t b = (m * n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  resid_form_kernel<<<(unsigned)std::max<int64_t>(b, 1), 256, 0, s>>>(m, n, AX, BX, lam, W);
+  RC_LAUNCH();
+}
+}  // namespace rchfsi
+
+extern "C" {
+
+int rchfsi_params_default(rchfsi_params* p) {
+  if (!p) return RCHFSI_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->nev = 1;
+  p->block = 1;
+  p->degree = 20;
+  p->precision = RCHFSI_FP64;
+  p->method = RCHFSI_METHOD_RCHFSI;
+  p->field = RCHFSI_REAL;
+  p->max_iter = 100;
+  p->min_iter = 0;
+  p->lanczos_steps = 10;
+  p->stall_iters = 0;
+  p->fixed_bounds = 0;
+  p->tol = 1e-8;
+  return RCHFSI_OK;
+}
+
+int rchfsi_create(rchfsi_ctx** out, const rchfsi_params* p, void* cuda_stream) {
+  if (!out) return RCHFSI_ERR_INVALID_ARG;
+  *out = nullptr;
+  rchfsi_ctx* h = new rchfsi_ctx();
+  const int rc = guarded(h, [&] {
+    validate_params(p);
+    h->p = *p;
+    RC_CUDA(cudaGetDevice(&h->device));
+    RC_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (cuda_stream) {
+      h->s = (cudaStream_t)cuda_stream;
+    } else {
+      RC_CUDA(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+      h->own_stream = true;
+    }
+    for (auto& e : h->ev) RC_CUDA(cudaEventCreate(&e));
+    h->w.ensure(p->m, p->block);
+    return RCHFSI_OK;
+  });
+  if (rc != RCHFSI_OK) {
+    rchfsi_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return RCHFSI_OK;
+}
+
+int rchfsi_destroy(rchfsi_ctx* h) {
+  if (!h) return RCHFSI_OK;
+  if (h->s) cudaStreamSynchronize(h->s);
+  if (h->solver) cusolverDnDestroy(h->solver);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  cudaStream_t s = h->s;
+  bool own = h->own_stream;
+  delete h;
+  if (own && s) cudaStreamDestroy(s);
+  return RCHFSI_OK;
+}
+
+int rchfsi_set_params(rchfsi_ctx* h, const rchfsi_params* p) {
+  if (!h) return RCHFSI_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    validate_params(p);
+    RC_CHECK(p->m == h->p.m && p->block == h->p.block && p->field == h->p.field, RCHFSI_ERR_INVALID_ARG,
+             "m, block and field cannot change on an existing handle");
+    h->p = *p;
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_set_operator(rchfsi_ctx* h, const rchfsi_operator* op) {
+  if (!h) return RCHFSI_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    RC_CHECK(op, RCHFSI_ERR_INVALID_ARG, "operator is NULL");
+    RC_CHECK(op->m == h->p.m, RCHFSI_ERR_INVALID_ARG, "operator m differs from params m");
+    RC_CHECK(op->field == RCHFSI_REAL, RCHFSI_ERR_UNSUPPORTED, "complex Hermitian operators are not implemented");
+    h->has_op = false;
+    if (op->kind == RCHFSI_OP_DENSE) {
+      h->fe.reset();
+      set_dense(*h, op);
+    } else if (op->kind == RCHFSI_OP_FE_CELL) {
+      h->dense.reset();
+      set_fe(*h, op);
+    } else {
+      throw Error(RCHFSI_ERR_INVALID_ARG, "unknown operator kind");
+    }
+    h->op_kind = op->kind;
+    h->has_op = true;
+    if (h->p.hbm_budget_bytes && device_bytes(*h) > h->p.hbm_budget_bytes) {
+      h->has_op = false;
+      throw Error(RCHFSI_ERR_OOM, "operator does not fit in hbm_budget_bytes");
+    }
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_filter(rchfsi_ctx* h, const double* X, const double* Lambda, const double* W, double lmin, double lT,
+                  double lmax, int degree, double* Yp) {
+  return guarded(h, [&] {
+    need_op(h);
+    RC_CHECK(Yp, RCHFSI_ERR_INVALID_ARG, "Yp is NULL");
+    rchfsi_ctx& c = *h;
+    const std::vector<double> lam = host_vec(c, Lambda, c.p.block);
+    load_block(c, X, c.w.X.p);
+    load_block(c, W, c.w.W.p);
+    filter_internal(c, c.w.X.p, lam.data(), c.w.W.p, lmin, lT, lmax, degree, c.w.Y.p, false);
+    store_block(c, c.w.Y.p, Yp);
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_chfsi_filter(rchfsi_ctx* h, const double* X, double lmin, double lT, double lmax, int degree,
+                        double* Yp) {
+  return guarded(h, [&] {
+    need_op(h);
+    RC_CHECK(Yp, RCHFSI_ERR_INVALID_ARG, "Yp is NULL");
+    rchfsi_ctx& c = *h;
+    load_block(c, X, c.w.X.p);
+    filter_internal(c, c.w.X.p, nullptr, nullptr, lmin, lT, lmax, degree, c.w.Y.p, true);
+    store_block(c, c.w.Y.p, Yp);
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_residual(rchfsi_ctx* h, const double* X, const double* Lambda, double* W, double* rnorm) {
+  return guarded(h, [&] {
+    need_op(h);
+    rchfsi_ctx& c = *h;
+    const int64_t m = c.p.m;
+    const int N = c.p.block;
+    load_block(c, X, c.w.X.p);
+    to_device(c, Lambda, c.w.evals.p, N);
+    apply_A_f64(c, c.w.X.p, c.w.AX.p, N);
+    apply_B_f64(c, c.w.X.p, c.w.BX.p, N);
+    resid_form_f64(c.s, m, N, c.w.AX.p, c.w.BX.p, c.w.evals.p, c.w.W.p);
+    store_block(c, c.w.W.p, W);
+    if (rnorm) {
+      resid_rel_norms(c.s, m, N, c.w.W.p, c.w.X.p, c.w.rabs.p, c.w.xnrm.p);
+      from_device(c, c.w.rabs.p, rnorm, N);
+    }
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_rayleigh_ritz(rchfsi_ctx* h, const double* Y, double* X, double* evals) {
+  return guarded(h, [&] {
+    need_op(h);
+    rchfsi_ctx& c = *h;
+    load_block(c, Y, c.w.Y.p);
+    const int rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
+    if (rc != RCHFSI_OK) return rc;
+    store_block(c, c.w.X.p, X);
+    from_device(c, c.w.evals.p, evals, c.p.block);
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_lanczos_bounds(rchfsi_ctx* h, const double* v0, int steps, double* lmax, double* normA) {
+  return guarded(h, [&] {
+    need_op(h);
+    rchfsi_ctx& c = *h;
+    double* v = c.w.T1.p;
+    to_device(c, v0, v, c.p.m);
+    lanczos(c, v, steps, lmax, normA);
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_solve(rchfsi_ctx* h, double* X_inout, double* evals, double* resid, rchfsi_stats* st) {
+  return guarded(h, [&] {
+    need_op(h);
+    rchfsi_ctx& c = *h;
+    const rchfsi_params& p = c.p;
+    const int64_t m = p.m;
+    const int N = p.block;
+    Work& w = c.w;
+    RC_CHECK(X_inout, RCHFSI_ERR_INVALID_ARG, "X_inout is NULL");
+    double* hist = st ? st->history : nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    double t_filter = 0.0, t_rr = 0.0;
+    auto ms_since = [](std::chrono::steady_clock::time_point a) {
+      return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+    };
+    load_block(c, X_inout, w.Y.p);
+    // bounds: Lanczos from the first column of the initial block (contiguous in column-major)
+    double lmax = p.lmax, normA = 1.0;
+    lanczos(c, w.Y.p, p.lanczos_steps, p.fixed_bounds ? nullptr : &lmax, &normA);
+    RC_CHECK(normA > 0.0 && std::isfinite(normA), RCHFSI_ERR_NUMERIC, "||A|| estimate is not positive");
+    auto tr = std::chrono::steady_clock::now();
+    int rc = rayleigh_ritz(c, w.Y.p, w.X.p, w.AX.p, w.BX.p, w.evals.p);
+    t_rr += ms_since(tr);
+    int it = 0;
+    double best = INFINITY;
+    int best_it = 0;
+    double maxrel = INFINITY, maxabs = INFINITY;
+    std::vector<double> ev(N), ra(N), xn(N);
+    int64_t applies = 0;
+    double flops = 0.0;
+    while (rc == RCHFSI_OK) {
+      tr = std::chrono::steady_clock::now();
+      resid_form_f64(c.s, m, N, w.AX.p, w.BX.p, w.evals.p, w.W.p);
+      resid_rel_norms(c.s, m, N, w.W.p, w.X.p, w.rabs.p, w.xnrm.p);
+      RC_CUDA(cudaMemcpyAsync(ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      RC_CUDA(cudaMemcpyAsync(ra.data(), w.rabs.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      RC_CUDA(cudaMemcpyAsync(xn.data(), w.xnrm.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      RC_CUDA(cudaStreamSynchronize(c.s));
+      t_rr += ms_since(tr);
+      maxrel = 0.0;
+      maxabs = 0.0;
+      bool finite = true;
+      for (int j = 0; j < p.nev; ++j) {
+        finite = finite && std::isfinite(ra[j]) && std::isfinite(ev[j]);
+        maxrel = std::max(maxrel, ra[j] / (normA * xn[j]));
+        maxabs = std::max(maxabs, ra[j]);
+      }
+      if (hist && it <= p.max_iter) hist[it] = maxrel;
+      if (!finite) {
+        rc = RCHFSI_ERR_NUMERIC;
+        break;
+      }
+      if (maxrel <= p.tol && it >= p.min_iter) break;
+      if (it >= p.max_iter) {
+        rc = RCHFSI_ERR_NOT_CONVERGED;
+        break;
+      }
+      if (maxrel < 0.5 * best) {
+        best = maxrel;
+        best_it = it;
+      } else if (p.stall_iters > 0 && it - best_it >= p.stall_iters) {
+        rc = RCHFSI_ERR_STAGNATED;
+        break;
+      }
+      const double lmin = p.fixed_bounds ? p.lmin : ev[0];
+      const double lT = p.fixed_bounds ? p.lT : ev[N - 1];
+      const double lmx = p.fixed_bounds ? p.lmax : lmax;
+      const auto tf = std::chrono::steady_clock::now();
+      filter_internal(c, w.X.p, ev.data(), w.W.p, lmin, lT, lmx, p.degree, w.Y.p,
+                      p.method == RCHFSI_METHOD_CHFSI);
+      t_filter += ms_since(tf);
+      applies += c.last_applies;
+      flops += c.last_flops;
+      tr = std::chrono::steady_clock::now();
+      rc = rayleigh_ritz(c, w.Y.p, w.X.p, w.AX.p, w.BX.p, w.evals.p);
+      t_rr += ms_since(tr);
+      ++it;
+    }
+    store_block(c, w.X.p, X_inout);
+    from_device(c, w.evals.p, evals, N);
+    if (resid) {
+      std::vector<double> rel(N);
+      for (int j = 0; j < N; ++j) rel[j] = ra[j] / (normA * xn[j]);
+      const auto kind = is_device_pointer(resid) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+      RC_CUDA(cudaMemcpyAsync(resid, rel.data(), N * sizeof(double), kind, c.s));
+    }
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    if (st) {
+      st->iterations = it;
+      st->status = rc;
+      st->max_rel_residual = maxrel;
+      st->max_abs_residual = maxabs;
+      st->lmax = lmax;
+      st->normA = normA;
+      st->t_total_ms = ms_since(t0);
+      st->t_filter_ms = t_filter;
+      st->t_rr_ms = t_rr;
+      st->filter_flops = flops;
+      st->operator_applies = applies;
+    }
+    return rc;
+  });
+}
+
+const char* rchfsi_strerror(int code) {
+  switch (code) {
+    case RCHFSI_OK: return "ok";
+    case RCHFSI_PENDING: return "pending";
+    case RCHFSI_ERR_INVALID_ARG: return "invalid argument";
+    case RCHFSI_ERR_OOM: return "out of device memory or over the HBM budget";
+    case RCHFSI_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case RCHFSI_ERR_STAGNATED: return "residual stagnated";
+    case RCHFSI_ERR_ILL_CONDITIONED: return "Gram matrix not positive definite";
+    case RCHFSI_ERR_NUMERIC: return "non-finite value";
+    case RCHFSI_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RCHFSI_ERR_CUDA: return "CUDA error";
+    case RCHFSI_ERR_NO_OPERATOR: return "no operator set";
+    case RCHFSI_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int rchfsi_last_error(rchfsi_ctx* h, char* buf, size_t len) {
+  if (!buf || len == 0) return RCHFSI_ERR_INVALID_ARG;
+  const std::string& s = h ? h->err : g_last_error;
+  const size_t n = std::min(len - 1, s.size());
+  std::memcpy(buf, s.data(), n);
+  buf[n] = 0;
+  return RCHFSI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,609 @@
+// C ABI of the R-ChFSI library and the host-side drivers of Algorithms 1-3.
+//
+// Host code computes the O(p) Chebyshev scalars and the O(pN) table of Lambda_k (the eigenvalue
+// recurrence of Proposition 3.3) in FP64 and uploads them once per filter, so the whole degree
+// loop is enqueued on the stream without host round trips.  Everything that touches an m-sized
+// array runs in this library's kernels.
+#include <cuda.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "solver.cuh"
+#include "tc_gemm.cuh"
+
+using namespace rchfsi;
+
+namespace rchfsi {
+
+void Work::ensure(int64_t m_, int N_) {
+  if (m_ == m && N_ == N && X.p) return;
+  m = m_;
+  N = N_;
+  const size_t blk = (size_t)m * N;
+  X.ensure(blk); AX.ensure(blk); BX.ensure(blk); W.ensure(blk); Y.ensure(blk); AY.ensure(blk); BY.ensure(blk);
+  T1.ensure(blk);
+  GA.ensure((size_t)N * N); GB.ensure((size_t)N * N); Z.ensure((size_t)N * N); Zt.ensure((size_t)N * N);
+  evals.ensure(N); nrm.ensure(N); rabs.ensure(N); xnrm.ensure(N);
+  info.ensure(4);
+  RC_CUDA(cudaMemset(info.p, 0, 4 * sizeof(int)));
+}
+
+bool has_B(const rchfsi_ctx& c) {
+  if (c.op_kind == RCHFSI_OP_DENSE) return c.dense.has_B;
+  return true;
+}
+
+const double* dinv_diag(const rchfsi_ctx& c) {
+  if (c.op_kind == RCHFSI_OP_DENSE) return c.dense.has_dinv ? c.dense.Dinv.p : nullptr;
+  return c.fe->Dinv.p;
+}
+
+static EpiArgs epi_store(void* C, int64_t ldc) {
+  EpiArgs e;
+  e.kind = EPI_STORE;
+  e.C = C;
+  e.ldc = ldc;
+  return e;
+}
+
+// Row-major <-> column-major for FE applies on column-major solver blocks.
+static void fe_apply_cols(rchfsi_ctx& c, bool useB, const double* X, double* Y, int n) {
+  const int64_t m = c.p.m;
+  double* xr = c.w.stage_in.ensure((size_t)m * n);
+  double* yr = c.w.stage_out.ensure((size_t)m * n);
+  transpose_f64(c.s, n, m, X, m, xr, n);  // X col-major = n x m row-major view -> m x n row-major
+  fe_apply_f64_rows(c.s, *c.fe, useB, xr, yr, n);
+  transpose_f64(c.s, m, n, yr, n, Y, m);
+}
+
+void apply_A_f64(rchfsi_ctx& c, const double* X, double* Y, int n) {
+  const int64_t m = c.p.m;
+  if (c.op_kind == RCHFSI_OP_DENSE) {
+    gemm_f64(c.s, m, n, m, c.dense.A.p, m, true, X, m, true, epi_store(Y, m));
+  } else {
+    fe_apply_cols(c, false, X, Y, n);
+  }
+}
+
+void apply_B_f64(rchfsi_ctx& c, const double* X, double* Y, int n) {
+  const int64_t m = c.p.m;
+  if (c.op_kind == RCHFSI_OP_DENSE) {
+    if (c.dense.has_B)
+      gemm_f64(c.s, m, n, m, c.dense.B.p, m, true, X, m, true, epi_store(Y, m));
+    else
+      RC_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, c.s));
+  } else {
+    fe_apply_cols(c, true, X, Y, n);
+  }
+}
+
+size_t device_bytes(const rchfsi_ctx& c) {
+  size_t t = 0;
+  const DenseOp& d = c.dense;
+  t += d.A.bytes() + d.B.bytes() + d.Dinv.bytes() + d.Dinv_dense.bytes() + d.AD64.bytes() + d.DA64.bytes();
+  t += d.AD32.bytes() + d.DA32.bytes() + d.ADtf.bytes() + d.DAtf.bytes() + d.AD16.bytes() + d.DA16.bytes();
+  if (c.fe) {
+    const FeOp& f = *c.fe;
+    t += f.dofs.bytes() + f.A64.bytes() + f.B64.bytes() + f.Dinv.bytes() + f.A32.bytes() + f.Atf.bytes() +
+         f.A16.bytes() + f.Dinv32.bytes();
+  }
+  const Work& w = c.w;
+  t += w.X.bytes() * 8 + w.GA.bytes() * 4 + w.R32a.bytes() * 3 + w.R16a.bytes() * 3 + w.split.bytes() +
+       w.stage_in.bytes() + w.stage_out.bytes() + w.lamtab.bytes();
+  return t;
+}
+
+static void check_budget(rchfsi_ctx& c) {
+  if (c.p.hbm_budget_bytes && device_bytes(c) > c.p.hbm_budget_bytes)
+    throw Error(RCHFSI_ERR_OOM, "device footprint " + std::to_string(device_bytes(c)) +
+                                    " bytes exceeds hbm_budget_bytes " + std::to_string(c.p.hbm_budget_bytes));
+}
+
+// ------------------------------------------------------------------ low-precision operator copies
+// Reduced-precision dense operands use a row pitch padded to a multiple of 8 elements, so that
+// every row starts on a 16-byte boundary (a TMA requirement); padding is zero-filled.
+static inline int64_t padded(int64_t m) { return (m + 7) / 8 * 8; }
+
+static const float* dense_op32(rchfsi_ctx& c, bool chfsi, bool tf32) {
+  DenseOp& d = c.dense;
+  const int64_t m = c.p.m, mp = padded(m);
+  DevBuf<float>& buf = chfsi ? (tf32 ? d.DAtf : d.DA32) : (tf32 ? d.ADtf : d.AD32);
+  if (!buf.p) {
+    buf.ensure((size_t)m * mp);
+    fill_zero(c.s, buf.p, buf.bytes());
+    cast2d_f64_to_f32(c.s, m, m, chfsi ? d.DA64.p : d.AD64.p, m, buf.p, mp, 1.0, tf32 ? 1 : 0);
+    check_budget(c);
+  }
+  return buf.p;
+}
+
+static const __nv_bfloat16* dense_op16(rchfsi_ctx& c, bool chfsi) {
+  DenseOp& d = c.dense;
+  const int64_t m = c.p.m, mp = padded(m);
+  DevBuf<__nv_bfloat16>& buf = chfsi ? d.DA16 : d.AD16;
+  if (!buf.p) {
+    buf.ensure((size_t)m * mp);
+    fill_zero(c.s, buf.p, buf.bytes());
+    cast2d_f64_to_bf16(c.s, m, m, chfsi ? d.DA64.p : d.AD64.p, m, buf.p, mp, 1.0);
+    check_budget(c);
+  }
+  return buf.p;
+}
+
+// ------------------------------------------------------------------ the filters
+struct Coef {
+  double a, b, c;
+};
+
+static void filter_scalars(double lmin, double lT, double lmax, int p, double& e, double& cc, double& s1,
+                           std::vector<Coef>& co) {
+  // Algorithms 2/3, first line: e, c, sigma_1, gamma; loop k = 2..p: sigma_2 = 1/(gamma - sigma)
+  e = 0.5 * (lmax - lT);
+  cc = 0.5 * (lmax + lT);
+  s1 = e / (lmin - cc);
+  const double gamma = 2.0 / s1;
+  double sigma = s1;
+  co.clear();
+  for (int k = 2; k <= p; ++k) {
+    const double s2 = 1.0 / (gamma - sigma);
+    const double a = 2.0 * s2 / e;
+    co.push_back({a, -a * cc, -sigma * s2});
+    sigma = s2;
+  }
+}
+
+// Lambda_d = C_d(Lambda) for d = 0..p (Proposition 3.3), row d of the (p+1) x N table.
+static void lambda_table(const double* lam, int N, double e, double cc, double s1, const std::vector<Coef>& co,
+                         std::vector<double>& tab) {
+  const int p = (int)co.size() + 1;
+  tab.assign((size_t)(p + 1) * N, 0.0);
+  for (int j = 0; j < N; ++j) {
+    double lx = 1.0, ly = (s1 / e) * (lam[j] - cc);
+    tab[j] = 1.0;
+    tab[(size_t)N + j] = ly;
+    for (int k = 0; k < p - 1; ++k) {
+      const double a = co[k].a;
+      const double nx = a * ly * lam[j] - a * cc * ly + co[k].c * lx;
+      lx = ly;
+      ly = nx;
+      tab[(size_t)(k + 2) * N + j] = ly;
+    }
+  }
+}
+
+static void check_bounds(double lmin, double lT, double lmax, int p) {
+  RC_CHECK(p >= 1, RCHFSI_ERR_INVALID_ARG, "degree must be >= 1");
+  RC_CHECK(std::isfinite(lmin) && std::isfinite(lT) && std::isfinite(lmax), RCHFSI_ERR_INVALID_ARG,
+           "bounds must be finite");
+  RC_CHECK(lmax > lT, RCHFSI_ERR_INVALID_ARG, "need lmax > lT");
+  RC_CHECK(lmin < lT, RCHFSI_ERR_INVALID_ARG, "need lmin < lT");
+}
+
+// Dense filter product step for the reduced precisions on column-major FP32/BF16 blocks of pitch mp.
+static void dense_step_lowp(rchfsi_ctx& c, bool chfsi, int prec, const void* Ry, const void* Rx, const void* W,
+                            const double* lam, const Coef& k, void* out) {
+  const int64_t m = c.p.m, mp = padded(m);
+  const int N = c.p.block;
+  if (prec == RCHFSI_FP32) {
+    EpiArgs e;
+    e.kind = EPI_RECUR;
+    e.C = out;
+    e.ldc = mp;
+    e.a = k.a;
+    e.b = k.b;
+    e.c = k.c;
+    e.Ry = Ry;
+    e.Rx = Rx;
+    e.W = W;
+    e.lam = lam;
+    gemm_f32(c.s, m, N, m, dense_op32(c, chfsi, false), mp, true, (const float*)Ry, mp, true, e);
+  } else if (prec == RCHFSI_TF32) {
+    TcRecur r{(float)k.a, (float)k.b, (float)k.c, (const float*)Ry, (const float*)Rx, (const float*)W, lam,
+              (float*)out};
+    tc_gemm_tf32_recur(c.s, c.num_sms, m, N, m, dense_op32(c, chfsi, true), mp, (const float*)Ry, mp, c.w.split,
+                       r, mp, c.w.info.p + 2);
+  } else {
+    TcRecur16 r{(float)k.a, (float)k.b, (float)k.c, (const __nv_bfloat16*)Ry, (const __nv_bfloat16*)Rx,
+                (const __nv_bfloat16*)W, lam, (__nv_bfloat16*)out};
+    tc_gemm_bf16_recur(c.s, c.num_sms, m, N, m, dense_op16(c, chfsi), mp, (const __nv_bfloat16*)Ry, mp, c.w.split,
+                       r, mp, c.w.info.p + 2);
+  }
+}
+
+static void filter_dense(rchfsi_ctx& c, const double* X, const double* W, int p, const double* lamtab, double e,
+                         double cc, double s1, const std::vector<Coef>& co, double* Y, bool chfsi) {
+  const int64_t m = c.p.m;
+  const int N = c.p.block;
+  const size_t blk = (size_t)m * N;
+  const int prec = c.p.precision;
+  DenseOp& d = c.dense;
+  const double* lam_p = lamtab + (size_t)p * N;
+  if (prec == RCHFSI_FP64) {
+    double* RX = c.w.AY.p;
+    double* RY = c.w.BY.p;
+    const double* op = chfsi ? d.DA64.p : d.AD64.p;
+    if (!chfsi) {
+      scaled_copy_f64(c.s, blk, W, RY, s1 / e);
+    } else {
+      // Algorithm 2: Y_0 = X, Y_1 = (sigma_1/e)(H - cI) X
+      RC_CUDA(cudaMemcpyAsync(RX, X, blk * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+      EpiArgs e1;
+      e1.kind = EPI_RECUR;
+      e1.C = RY;
+      e1.ldc = m;
+      e1.a = s1 / e;
+      e1.b = -(s1 / e) * cc;
+      e1.c = 0.0;
+      e1.Ry = X;
+      gemm_f64(c.s, m, N, m, op, m, true, X, m, true, e1);
+    }
+    for (size_t k = 0; k < co.size(); ++k) {
+      EpiArgs ep;
+      ep.kind = EPI_RECUR;
+      ep.C = RX;
+      ep.ldc = m;
+      ep.a = co[k].a;
+      ep.b = co[k].b;
+      ep.c = co[k].c;
+      ep.Ry = RY;
+      ep.Rx = (chfsi || k > 0) ? RX : nullptr;  // R_X = 0 before the first step of Algorithm 3
+      ep.W = chfsi ? nullptr : W;
+      ep.lam = chfsi ? nullptr : lamtab + (k + 1) * N;
+      gemm_f64(c.s, m, N, m, op, m, true, RY, m, true, ep);
+      std::swap(RX, RY);
+    }
+    if (chfsi) {
+      RC_CUDA(cudaMemcpyAsync(Y, RY, blk * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    } else if (d.has_dinv_dense) {
+      EpiArgs ep;
+      ep.kind = EPI_AXPY_DIAG;
+      ep.C = Y;
+      ep.ldc = m;
+      ep.Xadd = X;
+      ep.ldx = m;
+      ep.lam = lam_p;
+      gemm_f64(c.s, m, N, m, d.Dinv_dense.p, m, true, RY, m, true, ep);
+    } else {
+      reconstruct_f64(c.s, m, N, RY, m, d.has_dinv ? d.Dinv.p : nullptr, X, lam_p, Y);
+    }
+    c.last_applies = (int64_t)co.size() + (chfsi ? 1 : 0);
+    return;
+  }
+  // reduced precision: FP32 / TF32 storage in float, BF16 storage in bfloat16, pitch mp
+  const int64_t mp = padded(m);
+  const size_t pblk = (size_t)mp * N;
+  const bool bf = prec == RCHFSI_BF16;
+  void *RX, *RY, *Wl;
+  if (bf) {
+    const bool fresh = c.w.R16a.n < pblk;
+    RX = c.w.R16a.ensure(pblk);
+    RY = c.w.R16b.ensure(pblk);
+    Wl = c.w.W16.ensure(pblk);
+    if (fresh) {
+      fill_zero(c.s, RX, pblk * 2);
+      fill_zero(c.s, RY, pblk * 2);
+      fill_zero(c.s, Wl, pblk * 2);
+    }
+  } else {
+    const bool fresh = c.w.R32a.n < pblk;
+    RX = c.w.R32a.ensure(pblk);
+    RY = c.w.R32b.ensure(pblk);
+    Wl = c.w.W32.ensure(pblk);
+    if (fresh) {
+      fill_zero(c.s, RX, pblk * 4);
+      fill_zero(c.s, RY, pblk * 4);
+      fill_zero(c.s, Wl, pblk * 4);
+    }
+  }
+  check_budget(c);
+  // column-major m x N (pitch m) -> pitch mp: N "rows" of m contiguous entries
+  auto cast = [&](const double* in, void* out, double scale) {
+    if (bf) cast2d_f64_to_bf16(c.s, N, m, in, m, (__nv_bfloat16*)out, mp, scale);
+    else cast2d_f64_to_f32(c.s, N, m, in, m, (float*)out, mp, scale, 0);
+  };
+  auto recon = [&](const void* R, const double* dv, const double* lam, double* out) {
+    if (bf) reconstruct_bf16(c.s, m, N, (const __nv_bfloat16*)R, mp, dv, X, lam, out);
+    else reconstruct_f32(c.s, m, N, (const float*)R, mp, dv, X, lam, out);
+  };
+  if (!chfsi) {
+    cast(W, RY, s1 / e);
+    cast(W, Wl, 1.0);
+  } else {
+    cast(X, RX, 1.0);
+    dense_step_lowp(c, true, prec, RX, nullptr, nullptr, nullptr, Coef{s1 / e, -(s1 / e) * cc, 0.0}, RY);
+  }
+  for (size_t k = 0; k < co.size(); ++k) {
+    dense_step_lowp(c, chfsi, prec, RY, (chfsi || k > 0) ? RX : nullptr, chfsi ? nullptr : Wl,
+                    chfsi ? nullptr : lamtab + (k + 1) * N, co[k], RX);
+    std::swap(RX, RY);
+  }
+  if (chfsi) {
+    recon(RY, nullptr, c.w.nrm.p, Y);  // nrm holds zeros: plain upcast
+  } else if (d.has_dinv_dense) {
+    recon(RY, nullptr, c.w.nrm.p, c.w.T1.p);
+    EpiArgs ep;
+    ep.kind = EPI_AXPY_DIAG;
+    ep.C = Y;
+    ep.ldc = m;
+    ep.Xadd = X;
+    ep.ldx = m;
+    ep.lam = lam_p;
+    gemm_f64(c.s, m, N, m, d.Dinv_dense.p, m, true, c.w.T1.p, m, true, ep);
+  } else {
+    recon(RY, d.has_dinv ? d.Dinv.p : nullptr, lam_p, Y);
+  }
+  c.last_applies = (int64_t)co.size() + (chfsi ? 1 : 0);
+}
+
+static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, const double* lamtab, double e,
+                      double cc, double s1, const std::vector<Coef>& co, double* Y, bool chfsi) {
+  const int64_t m = c.p.m;
+  const int N = c.p.block;
+  const size_t blk = (size_t)m * N;
+  const int prec = c.p.precision;
+  FeOp& f = *c.fe;
+  // row-major working copy of the input block (W for Algorithm 3, X for Algorithm 2)
+  double* Wr = c.w.stage_out.ensure(blk);
+  transpose_f64(c.s, N, m, chfsi ? X : W, m, Wr, N);
+  if (prec == RCHFSI_FP64) {
+    double* RX = c.w.AY.p;
+    double* RY = c.w.BY.p;
+    if (!chfsi) {
+      scaled_copy_f64(c.s, blk, Wr, RY, s1 / e);
+    } else {
+      RC_CUDA(cudaMemcpyAsync(RX, Wr, blk * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+      recur_terms_rows_f64(c.s, m, N, RX, RY, nullptr, nullptr, 0.0, -(s1 / e) * cc, 0.0);
+      fe_filter_product_f64(c.s, f, RX, RY, N, s1 / e, 2);
+    }
+    for (size_t k = 0; k < co.size(); ++k) {
+      if (!chfsi && k == 0) fill_zero(c.s, RX, blk * sizeof(double));
+      recur_terms_rows_f64(c.s, m, N, RY, RX, chfsi ? nullptr : Wr, chfsi ? nullptr : lamtab + (k + 1) * N,
+                           co[k].a, co[k].b, co[k].c);
+      fe_filter_product_f64(c.s, f, RY, RX, N, co[k].a, chfsi ? 2 : 1);
+      std::swap(RX, RY);
+    }
+    // back to column-major, then Y = D^-1 R_Y + X Lambda_p (or Y = R_Y for ChFSI)
+    transpose_f64(c.s, m, N, RY, N, Y, m);
+    if (!chfsi) reconstruct_f64(c.s, m, N, Y, m, f.Dinv.p, X, lamtab + (size_t)p * N, Y);
+    c.last_applies = (int64_t)co.size() + (chfsi ? 1 : 0);
+    return;
+  }
+  RC_CHECK(prec == RCHFSI_FP32 || prec == RCHFSI_TF32 || prec == RCHFSI_BF16, RCHFSI_ERR_INVALID_ARG,
+           "bad precision");
+  float* RX = c.w.R32a.ensure(blk);
+  float* RY = c.w.R32b.ensure(blk);
+  float* Wl = c.w.W32.ensure(blk);
+  check_budget(c);
+  if (!chfsi) {
+    cast_f64_to_f32(c.s, blk, Wr, RY, s1 / e, 0);
+    cast_f64_to_f32(c.s, blk, Wr, Wl, 1.0, 0);
+  } else {
+    cast_f64_to_f32(c.s, blk, Wr, RX, 1.0, 0);
+    recur_terms_rows_f32(c.s, m, N, RX, RY, nullptr, nullptr, 0.0, -(s1 / e) * cc, 0.0);
+    fe_filter_product_f32(c.s, f, prec, RX, RY, N, (float)(s1 / e), 2);
+  }
+  for (size_t k = 0; k < co.size(); ++k) {
+    if (!chfsi && k == 0) fill_zero(c.s, RX, blk * sizeof(float));
+    recur_terms_rows_f32(c.s, m, N, RY, RX, chfsi ? nullptr : Wl, chfsi ? nullptr : lamtab + (k + 1) * N,
+                         co[k].a, co[k].b, co[k].c);
+    fe_filter_product_f32(c.s, f, prec, RY, RX, N, (float)co[k].a, chfsi ? 2 : 1);
+    std::swap(RX, RY);
+  }
+  cast_f32_to_f64(c.s, blk, RY, Wr);
+  transpose_f64(c.s, m, N, Wr, N, Y, m);
+  if (!chfsi) reconstruct_f64(c.s, m, N, Y, m, f.Dinv.p, X, lamtab + (size_t)p * N, Y);
+  c.last_applies = (int64_t)co.size() + (chfsi ? 1 : 0);
+}
+
+void filter_internal(rchfsi_ctx& c, const double* X, const double* lam_host, const double* W, double lmin, double lT,
+                     double lmax, int p, double* Y, bool chfsi) {
+  check_bounds(lmin, lT, lmax, p);
+  const int N = c.p.block;
+  double e, cc, s1;
+  std::vector<Coef> co;
+  filter_scalars(lmin, lT, lmax, p, e, cc, s1, co);
+  std::vector<double> tab;
+  if (!chfsi) {
+    lambda_table(lam_host, N, e, cc, s1, co, tab);
+  } else {
+    tab.assign((size_t)(p + 1) * N, 0.0);
+  }
+  double* dtab = c.w.lamtab.ensure(tab.size());
+  RC_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  // zero "lambda" vector used by reconstructions that only upcast
+  RC_CUDA(cudaMemsetAsync(c.w.nrm.p, 0, sizeof(double) * N, c.s));
+  if (c.op_kind == RCHFSI_OP_DENSE)
+    filter_dense(c, X, W, p, dtab, e, cc, s1, co, Y, chfsi);
+  else
+    filter_fe(c, X, W, p, dtab, e, cc, s1, co, Y, chfsi);
+  // the host table must outlive the async copy; then read the kernels' timeout flag
+  int flag = 0;
+  RC_CUDA(cudaMemcpyAsync(&flag, c.w.info.p + 2, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  if (flag) {
+    RC_CUDA(cudaMemsetAsync(c.w.info.p + 2, 0, sizeof(int), c.s));
+    throw Error(RCHFSI_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel ran out");
+  }
+  const double flops_per = (c.op_kind == RCHFSI_OP_DENSE)
+                               ? 2.0 * (double)c.p.m * (double)c.p.m * N
+                               : 2.0 * (double)c.fe->nc * c.fe->nc * (double)c.fe->n_cells * N;
+  c.last_flops = flops_per * (double)c.last_applies;
+}
+
+// ------------------------------------------------------------------ Rayleigh-Ritz (FP64)
+static void syevd(rchfsi_ctx& c, int n, double* A, double* w) {
+  if (!c.solver) {
+    RC_CHECK(cusolverDnCreate(&c.solver) == CUSOLVER_STATUS_SUCCESS, RCHFSI_ERR_CUDA, "cusolverDnCreate failed");
+  }
+  RC_CHECK(cusolverDnSetStream(c.solver, c.s) == CUSOLVER_STATUS_SUCCESS, RCHFSI_ERR_CUDA, "cusolverDnSetStream");
+  int lwork = 0;
+  RC_CHECK(cusolverDnDsyevd_bufferSize(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n, w,
+                                       &lwork) == CUSOLVER_STATUS_SUCCESS,
+           RCHFSI_ERR_CUDA, "syevd buffer query failed");
+  double* work = c.w.syev_work.ensure((size_t)std::max(lwork, 1));
+  RC_CHECK(cusolverDnDsyevd(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n, w, work, lwork,
+                            c.w.info.p + 1) == CUSOLVER_STATUS_SUCCESS,
+           RCHFSI_ERR_CUDA, "syevd failed");
+}
+
+int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, double* evals) {
+  const int64_t m = c.p.m;
+  const int N = c.p.block;
+  Work& w = c.w;
+  // column scaling to unit 2-norm (span unchanged)
+  col_norms_f64(c.s, m, N, Y, m, w.nrm.p);
+  // invert norms on device: reuse scale kernel through a tiny copy
+  {
+    std::vector<double> hn(N);
+    RC_CUDA(cudaMemcpyAsync(hn.data(), w.nrm.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    for (int j = 0; j < N; ++j) {
+      RC_CHECK(std::isfinite(hn[j]), RCHFSI_ERR_NUMERIC, "non-finite column in the filtered block");
+      RC_CHECK(hn[j] > 0.0, RCHFSI_ERR_ILL_CONDITIONED, "zero column in the filtered block");
+      hn[j] = 1.0 / hn[j];
+    }
+    RC_CUDA(cudaMemcpyAsync(w.nrm.p, hn.data(), N * sizeof(double), cudaMemcpyHostToDevice, c.s));
+    scale_cols_f64(c.s, m, N, Y, m, w.nrm.p);
+    RC_CUDA(cudaStreamSynchronize(c.s));
+  }
+  double* AY = w.AY.p;
+  double* BY = w.BY.p;
+  apply_A_f64(c, Y, AY, N);
+  apply_B_f64(c, Y, BY, N);
+  // G_A = Y^T A Y, G_B = Y^T B Y  (N x N, column-major)
+  gemm_f64(c.s, N, N, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
+  gemm_f64(c.s, N, N, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
+  symmetrize_f64(c.s, N, w.GA.p, N);
+  symmetrize_f64(c.s, N, w.GB.p, N);
+  cholesky_f64(c.s, N, w.GB.p, N, w.info.p);
+  int info = 0;
+  RC_CUDA(cudaMemcpyAsync(&info, w.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  if (info != 0) return RCHFSI_ERR_ILL_CONDITIONED;
+  // M = L^-1 G_A L^-T
+  trsm_lower_left_f64(c.s, N, N, w.GB.p, N, w.GA.p, N);
+  transpose_f64(c.s, N, N, w.GA.p, N, w.Z.p, N);
+  trsm_lower_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
+  symmetrize_f64(c.s, N, w.Z.p, N);
+  syevd(c, N, w.Z.p, evals);
+  // E = L^-T V
+  trsm_lower_trans_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
+  // X = Y E, AX = AY E, BX = BY E
+  gemm_f64(c.s, m, N, N, Y, m, false, w.Z.p, N, true, epi_store(X, m));
+  gemm_f64(c.s, m, N, N, AY, m, false, w.Z.p, N, true, epi_store(AX, m));
+  gemm_f64(c.s, m, N, N, BY, m, false, w.Z.p, N, true, epi_store(BX, m));
+  RC_CUDA(cudaMemcpyAsync(&info, w.info.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  if (info != 0) return RCHFSI_ERR_NUMERIC;
+  return RCHFSI_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos
+// Eigenvalues of the symmetric tridiagonal T (alpha, beta) by Sturm-sequence bisection.
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+    q = (a[i] - x) - (i ? bb / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+static double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int idx) {
+  double lo = 1e300, hi = -1e300;
+  const size_t k = a.size();
+  for (size_t i = 0; i < k; ++i) {
+    const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (sturm_count(a, b, mid) > idx) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+namespace {
+__global__ void lz_scale_kernel(int64_t n, const double* x, const double* d, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] = d ? x[i] * sqrt(d[i]) : x[i];
+}
+// w <- w - alpha v - beta_prev vp   (beta_prev given as its square; null on the first step)
+__global__ void lz_update_kernel(int64_t n, double* w, const double* v, const double* vp, const double* alpha,
+                                 const double* beta_prev_sq) {
+  const double a = *alpha, b = beta_prev_sq ? sqrt(*beta_prev_sq) : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    w[i] = w[i] - a * v[i] - b * vp[i];
+}
+// vp <- v, v <- w / sqrt(beta_sq)
+__global__ void lz_next_kernel(int64_t n, double* vp, double* v, const double* w, const double* beta_sq) {
+  const double b = sqrt(*beta_sq);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    vp[i] = v[i];
+    v[i] = w[i] / b;
+  }
+}
+}  // namespace
+
+// k Lanczos steps on S = D^1/2 A D^1/2 (dinv = diagonal of the approximate inverse D^-1, or null for
+// S = A).  Returns alpha[0..k) and beta[0..k) (beta_j = ||w_j||).
+static void lanczos_run(rchfsi_ctx& c, const double* v0, int k, const double* dinv, std::vector<double>& al,
+                        std::vector<double>& be) {
+  const int64_t m = c.p.m;
+  Work& w = c.w;
+  double* v = w.lz_v.ensure(m);
+  double* wv = w.lz_w.ensure(m);
+  double* vp = w.lz_vp.ensure(m);
+  double* t = w.lz_t.ensure(m);
+  double* ab = w.lz_ab.ensure(2 * (size_t)k + 2);  // alpha[0..k), beta^2[0..k), ||v0||^2
+  const unsigned nb = std::min<unsigned>(cdiv(m, 256), 1024);
+  dot_f64(c.s, m, v0, v0, ab + 2 * k);
+  RC_CUDA(cudaMemcpyAsync(wv, v0, m * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+  lz_next_kernel<<<nb, 256, 0, c.s>>>(m, vp, v, wv, ab + 2 * k);  // v = v0 / ||v0||
+  RC_LAUNCH();
+  RC_CUDA(cudaMemsetAsync(vp, 0, m * sizeof(double), c.s));
+  for (int j = 0; j < k; ++j) {
+    lz_scale_kernel<<<nb, 256, 0, c.s>>>(m, v, dinv, t);
+    RC_LAUNCH();
+    apply_A_f64(c, t, wv, 1);
+    lz_scale_kernel<<<nb, 256, 0, c.s>>>(m, wv, dinv, wv);
+    RC_LAUNCH();
+    dot_f64(c.s, m, v, wv, ab + j);
+    lz_update_kernel<<<nb, 256, 0, c.s>>>(m, wv, v, vp, ab + j, j ? ab + k + j - 1 : nullptr);
+    RC_LAUNCH();
+    dot_f64(c.s, m, wv, wv, ab + k + j);
+    lz_next_kernel<<<nb, 256, 0, c.s>>>(m, vp, v, wv, ab + k + j);
+    RC_LAUNCH();
+  }
+  std::vector<double> h(2 * (size_t)k);
+  RC_CUDA(cudaMemcpyAsync(h.data(), ab, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  al.assign(h.begin(), h.begin() + k);
+  be.resize(k);
+  for (int j = 0; j < k; ++j) be[j] = std::sqrt(h[k + j]);
+}
+
+void lanczos(rchfsi_ctx& c, const double* v0, int k, double* lmax, double* normA) {
+  RC_CHECK(k >= 2 && k <= c.p.m, RCHFSI_ERR_INVALID_ARG, "lanczos_steps must be in [2, m]");
+  std::vector<double> al, be;
+  if (lmax) {
+    lanczos_run(c, v0, k, dinv_diag(c), al, be);
+    *lmax = tridiag_eig(al, be, k - 1) + be[k - 1];
+  }
+  if (normA) {
+    lanczos_run(c, v0, k, nullptr, al, be);
+    *normA = std::max(std::fabs(tridiag_eig(al, be, 0)), std::fabs(tridiag_eig(al, be, k - 1)));
+  }
+}
+
+}  // namespace rchfsi

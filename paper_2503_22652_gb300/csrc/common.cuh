@@ -1,0 +1,152 @@
+// Shared internal definitions of the R-ChFSI CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <stdexcept>
+#include <vector>
+
+#include "../../include/rchfsi.h"
+
+namespace rchfsi {
+
+// Error raised inside the library; converted to a status code at the C ABI.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& msg) : std::runtime_error(msg), code(c) {}
+};
+
+#define RC_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw ::rchfsi::Error(RCHFSI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
+                                                 " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+  } while (0)
+
+#define RC_CHECK(cond, code, msg)                    \
+  do {                                               \
+    if (!(cond)) throw ::rchfsi::Error((code), (msg)); \
+  } while (0)
+
+#define RC_LAUNCH() RC_CUDA(cudaGetLastError())
+
+// Owning device buffer.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  // Ensure capacity for `count` elements (contents are not preserved on growth).
+  T* ensure(size_t count) {
+    if (count <= n && p) return p;
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error(RCHFSI_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+    return p;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+inline bool is_device_pointer(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------- kernels (launchers)
+// All matrices are dense; "col" = column-major (each column contiguous, leading dim = rows),
+// "row" = row-major.  Internal m x N blocks are column-major.
+
+// C = op(A) op(B) consumed by an epilogue.  A(i,k) at A[i*lda+k] if a_kcontig else A[k*lda+i];
+// B(k,j) at B[j*ldb+k] if b_kcontig else B[k*ldb+j].
+enum EpiKind { EPI_STORE = 0, EPI_RECUR = 1, EPI_AXPY_DIAG = 2, EPI_RESID = 3 };
+
+struct EpiArgs {
+  int kind = EPI_STORE;
+  // EPI_STORE:     C[j*ldc+i] = alpha*acc + beta*C[j*ldc+i]
+  // EPI_RECUR:     Rx = a*acc + b*Ry + c*Rx + a*W*lam[j]   (W may be null; Rx may equal out)
+  // EPI_AXPY_DIAG: C = acc + Xadd[j*ldx+i]*lam[j]           (reconstruction with dense D^-1)
+  // EPI_RESID:     C = Xadd - acc*lam[j]                    (W = AX - BX Lambda)
+  void* C = nullptr;
+  int64_t ldc = 0;
+  double alpha = 1.0, beta = 0.0;
+  double a = 0, b = 0, c = 0;
+  const void* Ry = nullptr;
+  const void* Rx = nullptr;
+  const void* W = nullptr;
+  const double* lam = nullptr;
+  const void* Xadd = nullptr;
+  int64_t ldx = 0;
+};
+
+void gemm_f64(cudaStream_t s, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool a_kcontig,
+              const double* B, int64_t ldb, bool b_kcontig, const EpiArgs& epi);
+void gemm_f32(cudaStream_t s, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, bool a_kcontig,
+              const float* B, int64_t ldb, bool b_kcontig, const EpiArgs& epi);
+
+// Elementwise / layout kernels.
+void transpose_f64(cudaStream_t s, int64_t rows, int64_t cols, const double* in, int64_t ldin, double* out,
+                   int64_t ldout);  // out(j,i) = in(i,j), both row-major views
+void scale_cols_f64(cudaStream_t s, int64_t m, int64_t n, double* X, int64_t ld, const double* scale);
+void col_norms_f64(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_t ld, double* out);
+void scale_rows_f64(cudaStream_t s, int64_t m, int64_t n, const double* in, double* out, const double* d,
+                    bool cols);  // out = diag(d)*in (cols=false) or in*diag(d) (cols=true); row-major m x n
+void cast_f64_to_f32(cudaStream_t s, int64_t n, const double* in, float* out, double scale, int round_tf32);
+void cast_f64_to_bf16(cudaStream_t s, int64_t n, const double* in, __nv_bfloat16* out, double scale);
+void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out);
+void fill_zero(cudaStream_t s, void* p, size_t bytes);
+void scaled_copy_f64(cudaStream_t s, int64_t n, const double* in, double* out, double scale);
+// Yp(col) = dinv .* R + X .* lam  (R of type float/double, col-major m x n)
+// (R has leading dimension ldr; X and Y have leading dimension m.)
+void reconstruct_f64(cudaStream_t s, int64_t m, int64_t n, const double* R, int64_t ldr, const double* dinv,
+                     const double* X, const double* lam, double* Y);
+void reconstruct_f32(cudaStream_t s, int64_t m, int64_t n, const float* R, int64_t ldr, const double* dinv,
+                     const double* X, const double* lam, double* Y);
+void reconstruct_bf16(cudaStream_t s, int64_t m, int64_t n, const __nv_bfloat16* R, int64_t ldr,
+                      const double* dinv, const double* X, const double* lam, double* Y);
+// 2D casts: `rows` rows of `cols` contiguous elements, pitches ldin / ldout (elements).
+void cast2d_f64_to_f32(cudaStream_t s, int64_t rows, int64_t cols, const double* in, int64_t ldin, float* out,
+                       int64_t ldout, double scale, int round_tf32);
+void cast2d_f64_to_bf16(cudaStream_t s, int64_t rows, int64_t cols, const double* in, int64_t ldin,
+                        __nv_bfloat16* out, int64_t ldout, double scale);
+// Recurrence update without a product (for FE: Rx = b*Ry + c*Rx + a*W*lam), generic storage
+void recur_axpby_f32(cudaStream_t s, int64_t m, int64_t n, const float* Ry, float* Rx, const float* W,
+                     const double* lam, double a, double b, double c);
+// Residual-norm helpers
+void resid_rel_norms(cudaStream_t s, int64_t m, int64_t n, const double* W, const double* X, double* out_abs,
+                     double* out_xnorm);
+
+// Small dense FP64 kernels (N x N, column-major).
+int cholesky_f64(cudaStream_t s, int n, double* A, int lda, int* d_info);  // lower, in place
+void trsm_lower_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
+void trsm_lower_trans_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
+void symmetrize_f64(cudaStream_t s, int n, double* A, int lda);
+
+// Lanczos vector helpers
+void dot_f64(cudaStream_t s, int64_t n, const double* x, const double* y, double* out);
+
+}  // namespace rchfsi

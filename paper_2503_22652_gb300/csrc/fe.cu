@@ -1,0 +1,134 @@
+// SIMT kernels of the finite-element (cell-matrix) operator.
+//
+// One CTA takes one cell and one tile of block columns: it gathers the cell's n_c rows of the
+// input block into shared memory (scaled by D^-1 when the product is A D^-1 R), multiplies by the
+// cell matrix (row i of A_c is read as a warp-wide broadcast) and scatter-adds the n_c output rows
+// with atomics (a dof shared by several cells receives one add per cell).  This is the FP64 path
+// (residuals, Rayleigh-Ritz) and the FP32 "FFMA" filter path; the tensor-core path lives in
+// fe_tc.cu.
+#include "fe.cuh"
+#include "fe_tc.cuh"
+
+namespace rchfsi {
+namespace {
+
+constexpr int NCMAX = 128;
+
+template <typename T, int TN>
+__global__ void __launch_bounds__(256) fe_cell_kernel(int nc, const int* __restrict__ dofs,
+                                                      const T* __restrict__ Acells, int64_t a_stride,
+                                                      const T* __restrict__ X, T* __restrict__ Y, int n, T alpha,
+                                                      const double* __restrict__ dinv, int dmode) {
+  __shared__ T xs[NCMAX][TN];
+  __shared__ int ids[NCMAX];
+  const int64_t cell = blockIdx.x;
+  const int j0 = blockIdx.y * TN;
+  const int tid = threadIdx.x;
+  const T* Ac = Acells + cell * a_stride;
+  for (int i = tid; i < nc; i += blockDim.x) ids[i] = dofs[cell * nc + i];
+  __syncthreads();
+  for (int e = tid; e < nc * TN; e += blockDim.x) {
+    const int i = e / TN, j = e % TN;
+    const int col = j0 + j;
+    T v = T(0);
+    if (col < n) {
+      const int g = ids[i];
+      v = X[(int64_t)g * n + col];
+      if (dmode == 1) v *= (T)dinv[g];
+    }
+    xs[i][j] = v;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  constexpr int PER = TN / 32;
+  for (int i = warp; i < nc; i += 8) {
+    T acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = T(0);
+    const T* arow = Ac + (int64_t)i * nc;
+    for (int k = 0; k < nc; ++k) {
+      const T a = arow[k];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) acc[q] = fma(a, xs[k][lane + 32 * q], acc[q]);
+    }
+    const int g = ids[i];
+    T sc = alpha;
+    if (dmode == 2) sc *= (T)dinv[g];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int col = j0 + lane + 32 * q;
+      if (col < n) atomicAdd(&Y[(int64_t)g * n + col], sc * acc[q]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void recur_rows_kernel(int64_t total, int n, const T* __restrict__ Ry, T* __restrict__ Rx,
+                                  const T* __restrict__ W, const double* __restrict__ lam, T a, T b, T c) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    T v = b * Ry[e];
+    if (c != T(0)) v += c * Rx[e];
+    if (W) v += a * W[e] * (T)lam[e % n];
+    Rx[e] = v;
+  }
+}
+
+inline unsigned blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T, int TN>
+void launch_cells(cudaStream_t s, const FeOp& op, const T* A, int64_t a_stride, const T* X, T* Y, int n, T alpha,
+                  int dmode) {
+  RC_CHECK(op.nc <= NCMAX, RCHFSI_ERR_INVALID_ARG, "n_c larger than 128");
+  RC_CHECK(op.n_cells <= 0x7fffffff, RCHFSI_ERR_INVALID_ARG, "too many cells");
+  dim3 grid((unsigned)op.n_cells, cdiv(n, TN));
+  RC_CHECK(grid.y <= 65535u, RCHFSI_ERR_INVALID_ARG, "block too wide");
+  fe_cell_kernel<T, TN><<<grid, 256, 0, s>>>(op.nc, op.dofs.p, A, a_stride, X, Y, n, alpha, op.Dinv.p, dmode);
+  RC_LAUNCH();
+}
+
+}  // namespace
+
+void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n) {
+  RC_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * op.m * n, s));
+  const double* M = useB ? op.B64.p : op.A64.p;
+  const int64_t stride = (useB && op.B_shared) ? 0 : (int64_t)op.nc * op.nc;
+  launch_cells<double, 32>(s, op, M, stride, X, Y, n, 1.0, 0);
+}
+
+void fe_filter_product_f64(cudaStream_t s, const FeOp& op, const double* Ry, double* Rx, int n, double a,
+                           int dmode) {
+  launch_cells<double, 32>(s, op, op.A64.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode);
+}
+
+void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
+                           int dmode) {
+  const size_t na = (size_t)op.n_cells * op.nc * op.nc;
+  if (precision == RCHFSI_FP32) {
+    if (!op.A32.p) {
+      op.A32.ensure(na);
+      cast_f64_to_f32(s, na, op.A64.p, op.A32.p, 1.0, 0);
+    }
+    launch_cells<float, 64>(s, op, op.A32.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode);
+    return;
+  }
+  fe_tc_product(s, op, precision, Ry, Rx, n, a, dmode);
+}
+
+void recur_terms_rows_f32(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
+                          const double* lam, double a, double b, double c) {
+  recur_rows_kernel<float><<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, (float)a, (float)b,
+                                                             (float)c);
+  RC_LAUNCH();
+}
+
+void recur_terms_rows_f64(cudaStream_t s, int64_t m, int n, const double* Ry, double* Rx, const double* W,
+                          const double* lam, double a, double b, double c) {
+  recur_rows_kernel<double><<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, a, b, c);
+  RC_LAUNCH();
+}
+
+}  // namespace rchfsi

@@ -1,0 +1,43 @@
+// Finite-element (cell-matrix) operator: A = sum_c P_c^T A_c P_c over n_cells cells of n_c dofs.
+// The paper evaluates this product cell by cell with batched dense GEMMs (Remark in Section 4.2);
+// here each kernel gathers a cell's rows of the block, multiplies by the cell matrix and
+// scatter-adds the result.
+#pragma once
+#include "common.cuh"
+
+namespace rchfsi {
+
+struct FeOp {
+  int64_t m = 0, n_cells = 0;
+  int nc = 0;
+  bool B_shared = false;
+  DevBuf<int> dofs;          // n_cells * nc
+  DevBuf<double> A64, B64;   // cell matrices, row-major (B64 holds one matrix when shared)
+  DevBuf<double> Dinv;       // m
+  DevBuf<float> A32;         // FP32 cell matrices for the filter products
+  DevBuf<float> Atf;         // TF32-rounded copy
+  DevBuf<__nv_bfloat16> A16; // BF16 copy
+  DevBuf<float> Dinv32;
+};
+
+// Y (row-major m x n) = Op X, Op = A or B, FP64.  Y is overwritten.
+void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n);
+
+// Filter product for FE operators on row-major m x n blocks, accumulated into Rx (the
+// product-free recurrence terms are applied to Rx beforehand):
+//   dmode 0: Rx += a * A Ry,  1: Rx += a * A D^-1 Ry (Algorithm 3),  2: Rx += a * D^-1 A Ry (Algorithm 2)
+// precision: RCHFSI_FP32 (FFMA), RCHFSI_TF32 / RCHFSI_BF16 (tensor cores).
+void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
+                           int dmode);
+
+// Same for FP64 storage (parity path).
+void fe_filter_product_f64(cudaStream_t s, const FeOp& op, const double* Ry, double* Rx, int n, double a,
+                           int dmode);
+
+// Elementwise recurrence terms for row-major blocks: Rx = b*Ry + c*Rx + a*W*lam[j]
+void recur_terms_rows_f32(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
+                          const double* lam, double a, double b, double c);
+void recur_terms_rows_f64(cudaStream_t s, int64_t m, int n, const double* Ry, double* Rx, const double* W,
+                          const double* lam, double a, double b, double c);
+
+}  // namespace rchfsi

@@ -1,0 +1,104 @@
+"""Parity of the finite-element (cell-matrix) operator path with the oracle, through the C ABI."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as wl
+from oracle import fe as ofe, filters, rr
+from gpu_helpers import ensure_built, relfro, round_mantissa
+
+from paper_2503_22652_gb300 import Solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    ensure_built()
+
+
+@pytest.fixture(scope="module")
+def fe3():
+    p = wl.fe_problem(3)          # 27 cells, 1728 dofs
+    A = ofe.assemble(p["cell_dofs"], p["A_cells"], p["m"])
+    B = ofe.assemble(p["cell_dofs"], p["B_cell"], p["m"])
+    return p, A, B
+
+
+def _inputs(p, A, B, N, seed=4):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((p["m"], N))
+    L = np.sort(rng.uniform(-20.0, 30.0, N))
+    W = A @ X - (B @ X) * L[None, :]
+    return X, L, W
+
+
+def _solver(p, N, precision="fp64", **kw):
+    s = Solver(p["m"], nev=max(1, N // 2), block=N, precision=precision, **kw)
+    s.set_fe(p["cell_dofs"], p["A_cells"], p["B_cell"], p["Dinv"])
+    return s
+
+
+@pytest.mark.parametrize("N", [1, 40, 70])
+def test_fe_residual_and_rr_parity(fe3, N):
+    p, A, B = fe3
+    X, L, W = _inputs(p, A, B, N)
+    s = _solver(p, N)
+    Wg, r = s.residual(X, L)
+    assert relfro(Wg, W) <= 1e-13
+    if N > 1:
+        Xg, ev = s.rayleigh_ritz(X)
+        _, evr, _, _ = rr.rayleigh_ritz(X, lambda v: A @ v, lambda v: B @ v)
+        np.testing.assert_allclose(ev, evr, rtol=1e-10, atol=1e-10 * np.abs(evr).max())
+
+
+@pytest.mark.parametrize("p_deg", [1, 2, 9])
+@pytest.mark.parametrize("method", ["rchfsi", "chfsi"])
+def test_fe_filter_fp64_parity(fe3, p_deg, method):
+    p, A, B = fe3
+    N = 40
+    X, L, W = _inputs(p, A, B, N)
+    d = p["Dinv"]
+    lmin, lT, lmax = -25.0, 40.0, 2500.0
+    s = _solver(p, N)
+    if method == "rchfsi":
+        ref = filters.rchfsi_filter(lambda R: A @ (d[:, None] * R), lambda R: d[:, None] * R, X, L, W,
+                                    lmin, lT, lmax, p_deg)
+        got = s.filter(X, L, W, lmin, lT, lmax, p_deg)
+    else:
+        ref = filters.chfsi_filter(lambda Y: d[:, None] * (A @ Y), X, lmin, lT, lmax, p_deg)
+        got = s.chfsi_filter(X, lmin, lT, lmax, p_deg)
+    assert relfro(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 5e-5), ("tf32", 5e-3), ("bf16", 5e-2)])
+def test_fe_filter_lowp(fe3, prec, tol):
+    """Reduced-precision FE filter against the FP64 oracle filter, error measured relative to the
+    part of Y_p produced by the low-precision recurrence, ||Y_p - X Lambda_p||."""
+    p, A, B = fe3
+    N = 48
+    X, L, W = _inputs(p, A, B, N)
+    d = p["Dinv"]
+    lmin, lT, lmax, deg = -25.0, 40.0, 2500.0, 8
+    ref = filters.rchfsi_filter(lambda R: A @ (d[:, None] * R), lambda R: d[:, None] * R, X, L, W,
+                                lmin, lT, lmax, deg)
+    base = X * filters.lambda_p(L, lmin, lT, lmax, deg)[None, :]
+    got = _solver(p, N, precision=prec).filter(X, L, W, lmin, lT, lmax, deg)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref - base)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32", "bf16"])
+def test_fe_solve_small_mesh(precision):
+    """Periodic 2^3 mesh with wells (512 dofs): R-ChFSI with the lumped-mass D^-1 converges to the
+    dense generalized eigenvalues in every precision."""
+    p = wl.fe_problem(2)
+    A = ofe.assemble(p["cell_dofs"], p["A_cells"], p["m"]).toarray()
+    B = ofe.assemble(p["cell_dofs"], p["B_cell"], p["m"]).toarray()
+    ref = sla.eigh(A, B, eigvals_only=True)[:7]
+    s = _solver(p, 12, precision=precision, degree=10, max_iter=150)
+    s.set_params(nev=7)
+    X0 = wl.gaussian_block(p["m"], 12, seed=2)
+    X, ev, res, st = s.solve(X0)
+    assert st["max_rel_residual"] <= 1e-8
+    np.testing.assert_allclose(ev[:7], ref, atol=1e-9 * np.abs(ref).max())
