@@ -1,0 +1,441 @@
+"""Benchmark of the R-ChFSI eigensolver on one GB300 (or N independent replicas).
+
+Default workload (the dense generalized benchmark problem): A = Q diag(lambda) Q^T with
+lambda = linspace(-1, 10) and a 0.05 gap after the 50th eigenvalue, m = 4000; dense SPD B with
+diag(B) log-uniform in [0.5, 50]; approximate inverse D^-1 = diag(B)^-1; nev = 200, block 240,
+degree 30; TF32 tensor-core filter products, FP64 residuals and Rayleigh-Ritz.  One step = one
+complete solve from the same seeded initial block to the relative residual 1e-8
+(time-to-tolerance).  `--workload fe` runs the finite-element problem instead (16^3 Q4 cells,
+262,144 dofs, nev 500, block 600, degree 25).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision tf32]
+
+Prints one JSON line (rank 0).  The reference arm (--impl reference) times the FP64 CPU oracle on
+this machine's host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+DENSE = dict(m=4000, nev=200, block=240, degree=30, tol=1e-8)
+FE = dict(n=16, nev=500, block=600, degree=25, tol=1e-8)
+METRIC = "R-ChFSI time-to-1e-8 relative residual"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "fe"])
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
+    return ap.parse_args()
+
+
+def workload_desc(kind, prec):
+    if kind == "dense":
+        return ("dense generalized A x = lambda B x, m=4000 (A: spectrum linspace(-1,10) + 0.05 gap after "
+                "index 50; B = S^1/2 (I + 0.1 G) S^1/2, diag(B)=S log-uniform[0.5,50]; D^-1 = diag(B)^-1), "
+                "nev=200, block=240, degree=30, %s filter products, FP64 Rayleigh-Ritz" % prec)
+    return ("FE generalized problem, periodic 16^3 Q4 cells (262,144 dofs), A = 0.5 K + V-mass (8 seeded "
+            "wells), B = consistent mass, D^-1 = GLL-lumped inverse, nev=500, block=600, degree=25, "
+            "%s filter products, FP64 Rayleigh-Ritz" % prec)
+
+
+def make_problem(kind):
+    if kind == "dense":
+        c = wl.dense_config2(m=DENSE["m"])
+        X0 = wl.gaussian_block(DENSE["m"], DENSE["block"], seed=2)
+        return {"dense": c, "X0": X0, **DENSE}
+    p = wl.fe_config3(n=FE["n"])
+    X0 = wl.gaussian_block(p["m"], FE["block"], seed=2)
+    return {"fe": p, "X0": X0, "m": p["m"], **FE}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def cpu_cores():
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        th = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if th:
+            return int(th[0])
+    except Exception:
+        pass
+    return n
+
+
+def oracle_sample(prob, iters=2):
+    """Time `iters` outer iterations (filter + Rayleigh-Ritz + residual) of the FP64 oracle
+    (Algorithm 1 with Algorithm 3) on the workload; returns seconds per outer iteration and the
+    time of the setup (Lanczos bounds + initial Rayleigh-Ritz)."""
+    from oracle import lanczos, rr, filters
+    X0 = prob["X0"]
+    if "dense" in prob:
+        c = prob["dense"]
+        A = lambda v: c["A"] @ v  # noqa: E731
+        B = lambda v: c["B"] @ v  # noqa: E731
+        d = c["Dinv"]
+    else:
+        from oracle import fe as ofe
+        p = prob["fe"]
+        As = ofe.assemble(p["cell_dofs"], p["A_cells"], p["m"])
+        Bs = ofe.assemble(p["cell_dofs"], p["B_cell"], p["m"])
+        A = lambda v: As @ v  # noqa: E731
+        B = lambda v: Bs @ v  # noqa: E731
+        d = p["Dinv"]
+    t0 = time.perf_counter()
+    lmax = lanczos.upper_bound(A, d, X0[:, 0], 10)
+    X, eps, AX, BX = rr.rayleigh_ritz(X0, A, B)
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for _ in range(iters):
+        W, _ = rr.residual(AX, BX, eps)
+        Y = filters.rchfsi_filter(lambda R: A(d[:, None] * R), lambda R: d[:, None] * R, X, eps, W, eps[0],
+                                  eps[-1], lmax, prob["degree"])
+        X, eps, AX, BX = rr.rayleigh_ritz(Y, A, B)
+    return (time.perf_counter() - t1) / iters, t_setup
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    prob = make_problem(args.workload)
+    iters_assumed = 10 if args.workload == "dense" else 8
+    samples = []
+    for _ in range(args.warmup):
+        oracle_sample(prob, iters=1)
+    for _ in range(args.steps):
+        per_it, setup = oracle_sample(prob, iters=1)
+        samples.append(setup + per_it * iters_assumed)
+    val = statistics.mean(samples) * 1e3
+    cores = cpu_cores()
+    desc = ("FP64 NumPy oracle: Lanczos bounds + initial Rayleigh-Ritz + 1 outer iteration timed per step, "
+            "scaled to %d outer iterations" % iters_assumed)
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "ms", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(val, 3), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc(args.workload, "fp64"), "parallelism": "host cores"},
+           "cpu_baseline": {"value": round(val, 3), "unit": "ms", "cores": cores, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": round(val, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return out
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline(prof, solve_ms_total, pk, precision):
+    """Roofline entry of the kernel class with the largest device time in the timed region."""
+    best = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, r = best
+    per_launch_ms = r["ms"] / max(r["launches"], 1)
+    hbm = pk.get("hbm_gbs", 6800.0)
+    bf16 = pk.get("bf16_tflops_sustained", 1700.0)
+    if name == "filter_tc":
+        # tensor-bound when the dense operator stays in L2 across the degree loop
+        ratio = {"tf32": 0.5, "bf16": 1.0}.get(precision, 0.5)
+        ach = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        peak = bf16 * ratio
+        return name, {"bound": "tensor", "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                      "frac": round(ach / peak, 4), "traffic": None,
+                      "peak_source": "measured bf16 sustained x nominal %s/bf16 ratio %.2f (of measured)" % (
+                          precision, ratio),
+                      "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
+    if name in ("gemm_f64", "filter_simt"):
+        ach = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        peak = 1.25 if name == "gemm_f64" else 69.8
+        return name, {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
+                      "frac": round(ach / peak, 4), "traffic": None,
+                      "peak_source": "nominal FP64 1.25 TFLOP/s" if name == "gemm_f64" else "FP32 FFMA",
+                      "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
+    ach = r["bytes"] / (r["ms"] * 1e-3) / 1e9
+    return name, {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                  "frac": round(ach / hbm, 4), "traffic": None, "peak_source": "measured HBM copy (of measured)",
+                  "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2503_22652_gb300 import Solver
+    import paper_2503_22652_gb300.build as B
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        B.build()
+    dev = torch.device("cuda", local_rank)
+    prob = make_problem(args.workload)
+    m, N = prob["m"], prob["block"]
+    stream = torch.cuda.current_stream()
+    s = Solver(m, nev=prob["nev"], block=N, degree=prob["degree"], precision=args.precision, max_iter=200,
+               tol=prob["tol"], stream=stream.cuda_stream)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    if "dense" in prob:
+        c = prob["dense"]
+        dA, dB, dD = T(c["A"]), T(c["B"]), T(c["Dinv"])
+        s.set_dense(dA, B=dB, Dinv=dD)
+    else:
+        p = prob["fe"]
+        s.set_fe(T(p["cell_dofs"]), T(p["A_cells"]), T(p["B_cell"]), T(p["Dinv"]))
+    X0 = T(prob["X0"])
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2 (flush buffer)
+
+    def one_solve():
+        X = X0.clone()
+        return s.solve(X)
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    s.profile(True)
+    times, iters, resid = [], [], []
+    for _ in range(args.steps):
+        l2.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, ev, res, st = one_solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters.append(st["iterations"])
+        resid.append(st["max_rel_residual"])
+    prof = {k: s.profile_read(k) for k in ("filter_tc", "splitk_reduce", "filter_simt", "gemm_f64", "fe_cell",
+                                           "fe_cell_f64")}
+    launches = s.profile_read("all")["launches"]
+    s.profile(False)
+    clocks = clk.stop()
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    ms = total / args.steps
+    st_last = st
+    pk = peaks()
+    kname, roof = roofline(prof, sum(times), pk, args.precision)
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = comparisons(s, prob, args, torch, dev, stream)
+    e2e = end_to_end(prob, args, torch) if rank == 0 else None
+    if rank != 0:
+        return None
+    sorted_t = sorted(times)
+    p99 = sorted_t[min(len(sorted_t) - 1, int(np.ceil(0.99 * len(sorted_t))) - 1)]
+    out = {"metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "%s+f64" % args.precision, "data": "synthetic",
+           "config": {"workload": workload_desc(args.workload, args.precision),
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "flushed (256 MB write) before every timed step"},
+           "p50_ms": round(statistics.median(times), 3), "p99_ms": round(p99, 3),
+           "solves_per_s": round(world * args.steps / (total * 1e-3), 3),
+           "iterations": iters[-1], "max_rel_residual": max(resid),
+           "t_filter_ms": round(st_last["t_filter_ms"], 3), "t_rr_ms": round(st_last["t_rr_ms"], 3),
+           "filter_tflops_in_solve": round(st_last["filter_flops"] / (st_last["t_filter_ms"] * 1e-3) / 1e12, 2),
+           "roofline_kernel": kname, "roofline": roof,
+           "kernel_classes_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
+           "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e}
+    out.update(extras)
+    out["cpu_baseline"] = cpu_baseline(prob, iters[-1])
+    return out
+
+
+def comparisons(s, prob, args, torch, dev, stream):
+    """Filter throughput of R-ChFSI in the chosen precision vs the FP64 ChFSI filter, and the FP64
+    R-ChFSI time-to-tolerance (one run each, outside the timed region)."""
+    out = {}
+    m, N, p = prob["m"], prob["block"], prob["degree"]
+    X = torch.from_numpy(np.linalg.qr(prob["X0"])[0]).to(dev)
+    lam = torch.linspace(-1.0, 0.5, N, dtype=torch.float64, device=dev)
+    W = torch.randn(m, N, dtype=torch.float64, device=dev) * 1e-3
+    bounds = (-1.5, 1.0, 80.0)
+    per = (2.0 * m * m * N) if "dense" in prob else 2.0 * 125 * 125 * prob["fe"]["cell_dofs"].shape[0] * N
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    t_r = timed(lambda: s.filter(X, lam, W, *bounds, p))
+    out["rchfsi_filter_ms"] = round(t_r, 3)
+    out["rchfsi_filter_tflops"] = round(per * (p - 1) / (t_r * 1e-3) / 1e12, 2)
+    s.set_params(precision="fp64")
+    t_c = timed(lambda: s.chfsi_filter(X, *bounds, p))
+    out["fp64_chfsi_filter_ms"] = round(t_c, 3)
+    out["fp64_chfsi_filter_tflops"] = round(per * p / (t_c * 1e-3) / 1e12, 3)
+    out["filter_speedup_vs_fp64_chfsi"] = round(t_c / t_r, 2)
+    Xs = torch.from_numpy(prob["X0"]).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, _, _, st = s.solve(Xs, allow_not_converged=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["fp64_rchfsi_time_ms"] = round(e0.elapsed_time(e1), 3)
+    out["fp64_rchfsi_iterations"] = st["iterations"]
+    s.set_params(precision=args.precision)
+    return out
+
+
+def end_to_end(prob, args, torch):
+    """Same solve through the C ABI with HOST (pinned) buffers: operator upload, initial block and
+    results cross PCIe/C2C inside the timed region."""
+    from paper_2503_22652_gb300 import Solver
+    m, N = prob["m"], prob["block"]
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64 if a.dtype == np.float64 else torch.int32, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    s = Solver(m, nev=prob["nev"], block=N, degree=prob["degree"], precision=args.precision, max_iter=200,
+               tol=prob["tol"])
+    if "dense" in prob:
+        c = prob["dense"]
+        args_op = dict(A=pinned(c["A"]), B=pinned(c["B"]), Dinv=pinned(c["Dinv"]))
+        h2d = sum(a.nbytes for a in args_op.values())
+        setop = lambda: s.set_dense(**args_op)  # noqa: E731
+    else:
+        p = prob["fe"]
+        ops = (pinned(p["cell_dofs"]), pinned(p["A_cells"]), pinned(p["B_cell"]), pinned(p["Dinv"]))
+        h2d = sum(a.nbytes for a in ops)
+        setop = lambda: s.set_fe(*ops)  # noqa: E731
+    X0 = pinned(prob["X0"])
+    h2d += X0.nbytes
+    d2h = X0.nbytes + 2 * N * 8
+    setop()
+    s.solve(X0)
+    ts = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        setop()
+        X, ev, res, st = s.solve(X0)
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    s.close()
+    return {"value": round(statistics.mean(ts), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "includes": "rchfsi_set_operator + rchfsi_solve from host buffers"}
+
+
+def cpu_baseline(prob, gpu_iters):
+    per_it, setup = oracle_sample(prob, iters=1)
+    val = (setup + per_it * gpu_iters) * 1e3
+    return {"value": round(val, 1), "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+            "sample": "FP64 NumPy oracle: Lanczos bounds + initial Rayleigh-Ritz + 1 outer iteration "
+                      "(filter + Rayleigh-Ritz + residual) timed, scaled to the GPU solve's %d iterations"
+                      % gpu_iters}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "gb300":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_gpu(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

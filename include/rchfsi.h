@@ -237,6 +237,30 @@ int rchfsi_submit(struct rchfsi_ctx* server, const rchfsi_request* rq, uint64_t*
  * buffers when given) and returns RCHFSI_OK; the ticket is then retired. */
 int rchfsi_poll(struct rchfsi_ctx* server, uint64_t ticket, rchfsi_result* out);
 
+/* ---------------------------------------------------------------- kernel timers */
+
+/* Kernel classes timed by the opt-in device timers. */
+typedef enum {
+  RCHFSI_KERNEL_FILTER_TC = 0,     /* tcgen05 dense filter product (TF32 / BF16) */
+  RCHFSI_KERNEL_SPLITK_REDUCE = 1, /* split-K reduction fused with the recurrence update */
+  RCHFSI_KERNEL_FILTER_SIMT = 2,   /* SIMT dense filter product (FP32 / FP64) */
+  RCHFSI_KERNEL_GEMM_F64 = 3,      /* FP64 GEMMs of the residual and Rayleigh-Ritz steps */
+  RCHFSI_KERNEL_FE_CELL = 4,       /* FE cell-matrix product inside the filter */
+  RCHFSI_KERNEL_FE_CELL_F64 = 5,   /* FE cell-matrix product of the residual / Rayleigh-Ritz (FP64) */
+  RCHFSI_KERNEL_CLASSES = 6
+} rchfsi_kernel_class;
+
+/* enable = 1: start timing every instrumented launch of this handle with CUDA events on the
+ * launching stream (previous records are cleared); enable = 0: stop and clear. */
+int rchfsi_profile(struct rchfsi_ctx* h, int enable);
+
+/* Totals for one kernel class since rchfsi_profile(h, 1): device time (ms), number of launches,
+ * and the algorithmic flops and bytes of those launches (each may be NULL).  Synchronises the
+ * handle's stream.  kernel_class = RCHFSI_KERNEL_CLASSES returns in *launches the number of all
+ * kernel launches of this library (any handle, any thread) since rchfsi_profile(h, 1). */
+int rchfsi_profile_read(struct rchfsi_ctx* h, int kernel_class, double* total_ms, int64_t* launches,
+                        double* flops, double* bytes);
+
 /* ---------------------------------------------------------------- errors */
 const char* rchfsi_strerror(int code);
 /* Copy the last error message of the handle (NUL-terminated, truncated to len). */

@@ -305,3 +305,22 @@ class Server:
         if X is not None:
             out["X"] = X
         return out
+
+
+def _solver_profile(self, enable=True):
+    """rchfsi_profile: start (True) or stop (False) the per-kernel-class device timers."""
+    self._check(self.lib.rchfsi_profile(self.h, 1 if enable else 0), self.h)
+
+
+def _solver_profile_read(self, cls):
+    """rchfsi_profile_read: dict(ms, launches, flops, bytes) of one kernel class ("all" = launch count)."""
+    idx = len(_lib.KERNEL_CLASSES) if cls == "all" else _lib.KERNEL_CLASSES[cls]
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int64()
+    self._check(self.lib.rchfsi_profile_read(self.h, idx, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by)),
+                self.h)
+    return {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+
+
+Solver.profile = _solver_profile
+Solver.profile_read = _solver_profile_read

@@ -28,6 +28,8 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
 METHOD_RCHFSI, METHOD_CHFSI = 0, 1
 REAL, COMPLEX = 0, 1
 OP_DENSE, OP_FE_CELL = 0, 1
+KERNEL_CLASSES = {"filter_tc": 0, "splitk_reduce": 1, "filter_simt": 2, "gemm_f64": 3, "fe_cell": 4,
+                  "fe_cell_f64": 5}
 
 dptr = C.POINTER(C.c_double)
 
@@ -86,6 +88,8 @@ SIGNATURES = {
     "rchfsi_server_destroy": (C.c_int, [C.c_void_p]),
     "rchfsi_submit": (C.c_int, [C.c_void_p, C.POINTER(rchfsi_request), C.POINTER(C.c_uint64)]),
     "rchfsi_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rchfsi_result)]),
+    "rchfsi_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "rchfsi_profile_read": (C.c_int, [C.c_void_p, C.c_int, dptr, C.POINTER(C.c_int64), dptr, dptr]),
     "rchfsi_strerror": (C.c_char_p, [C.c_int]),
     "rchfsi_last_error": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t]),
 }

@@ -14,12 +14,32 @@ void resid_form_f64(cudaStream_t s, int64_t m, int64_t n, const double* AX, cons
                     double* W);
 }
 
+namespace rchfsi {
+namespace prof {
+Profiler*& current() {
+  static thread_local Profiler* p = nullptr;
+  return p;
+}
+}  // namespace prof
+int64_t& launch_counter() {
+  static int64_t n = 0;
+  return n;
+}
+}  // namespace rchfsi
+
 namespace {
 
 thread_local std::string g_last_error;
 
+struct ProfBind {
+  prof::Profiler* prev;
+  explicit ProfBind(rchfsi_ctx* h) : prev(prof::current()) { prof::current() = h ? &h->prof : nullptr; }
+  ~ProfBind() { prof::current() = prev; }
+};
+
 template <class F>
 int guarded(rchfsi_ctx* h, F&& f) {
+  ProfBind pb(h);
   try {
     return f();
   } catch (const Error& e) {
@@ -186,6 +206,7 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
   const size_t nb = f.B_shared ? (size_t)f.nc * f.nc : na;
   to_device(c, op->B_cells, f.B64.ensure(nb), nb);
   to_device(c, op->Dinv, f.Dinv.ensure(c.p.m), c.p.m);
+  f.err = c.w.info.p + 2;
   RC_CUDA(cudaStreamSynchronize(c.s));
 }
 
@@ -486,6 +507,49 @@ int rchfsi_solve(rchfsi_ctx* h, double* X_inout, double* evals, double* resid, r
       st->operator_applies = applies;
     }
     return rc;
+  });
+}
+
+int rchfsi_profile(rchfsi_ctx* h, int enable) {
+  if (!h) return RCHFSI_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    if (h->s) RC_CUDA(cudaStreamSynchronize(h->s));
+    h->prof.clear();
+    h->prof.on = enable != 0;
+    h->prof.launch_base = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED);
+    return RCHFSI_OK;
+  });
+}
+
+int rchfsi_profile_read(rchfsi_ctx* h, int cls, double* total_ms, int64_t* launches, double* flops, double* bytes) {
+  if (!h) return RCHFSI_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    RC_CHECK(cls >= 0 && cls <= RCHFSI_KERNEL_CLASSES, RCHFSI_ERR_INVALID_ARG, "bad kernel class");
+    if (h->s) RC_CUDA(cudaStreamSynchronize(h->s));
+    if (cls == RCHFSI_KERNEL_CLASSES) {
+      // all kernel launches of this library (every thread) since rchfsi_profile(h, 1)
+      if (launches) *launches = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED) - h->prof.launch_base;
+      if (total_ms) *total_ms = 0.0;
+      if (flops) *flops = 0.0;
+      if (bytes) *bytes = 0.0;
+      return RCHFSI_OK;
+    }
+    double t = 0.0, fl = 0.0, by = 0.0;
+    int64_t n = 0;
+    for (const auto& r : h->prof.recs) {
+      if (r.cls != cls) continue;
+      float ms = 0.f;
+      RC_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      t += ms;
+      fl += r.flops;
+      by += r.bytes;
+      ++n;
+    }
+    if (total_ms) *total_ms = t;
+    if (launches) *launches = n;
+    if (flops) *flops = fl;
+    if (bytes) *bytes = by;
+    return RCHFSI_OK;
   });
 }
 

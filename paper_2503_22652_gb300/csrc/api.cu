@@ -200,6 +200,7 @@ static void dense_step_lowp(rchfsi_ctx& c, bool chfsi, int prec, const void* Ry,
     e.Rx = Rx;
     e.W = W;
     e.lam = lam;
+    e.prof_cls = RCHFSI_KERNEL_FILTER_SIMT;
     gemm_f32(c.s, m, N, m, dense_op32(c, chfsi, false), mp, true, (const float*)Ry, mp, true, e);
   } else if (prec == RCHFSI_TF32) {
     TcRecur r{(float)k.a, (float)k.b, (float)k.c, (const float*)Ry, (const float*)Rx, (const float*)W, lam,
@@ -239,6 +240,7 @@ static void filter_dense(rchfsi_ctx& c, const double* X, const double* W, int p,
       e1.b = -(s1 / e) * cc;
       e1.c = 0.0;
       e1.Ry = X;
+      e1.prof_cls = RCHFSI_KERNEL_FILTER_SIMT;
       gemm_f64(c.s, m, N, m, op, m, true, X, m, true, e1);
     }
     for (size_t k = 0; k < co.size(); ++k) {
@@ -253,6 +255,7 @@ static void filter_dense(rchfsi_ctx& c, const double* X, const double* W, int p,
       ep.Rx = (chfsi || k > 0) ? RX : nullptr;  // R_X = 0 before the first step of Algorithm 3
       ep.W = chfsi ? nullptr : W;
       ep.lam = chfsi ? nullptr : lamtab + (k + 1) * N;
+      ep.prof_cls = RCHFSI_KERNEL_FILTER_SIMT;
       gemm_f64(c.s, m, N, m, op, m, true, RY, m, true, ep);
       std::swap(RX, RY);
     }

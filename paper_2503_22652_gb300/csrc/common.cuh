@@ -31,7 +31,14 @@ struct Error : std::runtime_error {
     if (!(cond)) throw ::rchfsi::Error((code), (msg)); \
   } while (0)
 
-#define RC_LAUNCH() RC_CUDA(cudaGetLastError())
+// Count of this library's kernel launches (read through rchfsi_profile_read).
+int64_t& launch_counter();
+
+#define RC_LAUNCH()                                   \
+  do {                                                \
+    RC_CUDA(cudaGetLastError());                      \
+    __atomic_add_fetch(&::rchfsi::launch_counter(), 1, __ATOMIC_RELAXED); \
+  } while (0)
 
 // Owning device buffer.
 template <typename T>
@@ -101,6 +108,7 @@ struct EpiArgs {
   const double* lam = nullptr;
   const void* Xadd = nullptr;
   int64_t ldx = 0;
+  int prof_cls = RCHFSI_KERNEL_GEMM_F64;  // kernel class for the opt-in timers
 };
 
 void gemm_f64(cudaStream_t s, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool a_kcontig,

@@ -8,6 +8,7 @@
 // fe_tc.cu.
 #include "fe.cuh"
 #include "fe_tc.cuh"
+#include "prof.cuh"
 
 namespace rchfsi {
 namespace {
@@ -81,11 +82,14 @@ inline unsigned blocks_for(int64_t n) {
 
 template <typename T, int TN>
 void launch_cells(cudaStream_t s, const FeOp& op, const T* A, int64_t a_stride, const T* X, T* Y, int n, T alpha,
-                  int dmode) {
+                  int dmode, int cls) {
   RC_CHECK(op.nc <= NCMAX, RCHFSI_ERR_INVALID_ARG, "n_c larger than 128");
   RC_CHECK(op.n_cells <= 0x7fffffff, RCHFSI_ERR_INVALID_ARG, "too many cells");
   dim3 grid((unsigned)op.n_cells, cdiv(n, TN));
   RC_CHECK(grid.y <= 65535u, RCHFSI_ERR_INVALID_ARG, "block too wide");
+  const double nc = op.nc, C = (double)op.n_cells, es = sizeof(T);
+  // algorithmic bytes: input block read once, output block read+written once, the cell matrices
+  prof::Scope ps(s, cls, 2.0 * nc * nc * C * n, es * (3.0 * op.m * n + (a_stride ? C : 1.0) * nc * nc));
   fe_cell_kernel<T, TN><<<grid, 256, 0, s>>>(op.nc, op.dofs.p, A, a_stride, X, Y, n, alpha, op.Dinv.p, dmode);
   RC_LAUNCH();
 }
@@ -96,12 +100,12 @@ void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* 
   RC_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * op.m * n, s));
   const double* M = useB ? op.B64.p : op.A64.p;
   const int64_t stride = (useB && op.B_shared) ? 0 : (int64_t)op.nc * op.nc;
-  launch_cells<double, 32>(s, op, M, stride, X, Y, n, 1.0, 0);
+  launch_cells<double, 32>(s, op, M, stride, X, Y, n, 1.0, 0, RCHFSI_KERNEL_FE_CELL_F64);
 }
 
 void fe_filter_product_f64(cudaStream_t s, const FeOp& op, const double* Ry, double* Rx, int n, double a,
                            int dmode) {
-  launch_cells<double, 32>(s, op, op.A64.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode);
+  launch_cells<double, 32>(s, op, op.A64.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode, RCHFSI_KERNEL_FE_CELL);
 }
 
 void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
@@ -112,7 +116,7 @@ void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float*
       op.A32.ensure(na);
       cast_f64_to_f32(s, na, op.A64.p, op.A32.p, 1.0, 0);
     }
-    launch_cells<float, 64>(s, op, op.A32.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode);
+    launch_cells<float, 64>(s, op, op.A32.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode, RCHFSI_KERNEL_FE_CELL);
     return;
   }
   fe_tc_product(s, op, precision, Ry, Rx, n, a, dmode);

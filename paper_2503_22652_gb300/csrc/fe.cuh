@@ -18,6 +18,8 @@ struct FeOp {
   DevBuf<float> Atf;         // TF32-rounded copy
   DevBuf<__nv_bfloat16> A16; // BF16 copy
   DevBuf<float> Dinv32;
+  DevBuf<uint8_t> imgtf, img16;  // cell matrices packed as swizzled tensor-core operand images
+  int* err = nullptr;            // device flag raised when a bounded wait in a kernel runs out
 };
 
 // Y (row-major m x n) = Op X, Op = A or B, FP64.  Y is overwritten.

@@ -1,6 +1,334 @@
+// Finite-element filter product on the tcgen05 tensor cores:
+//   Rx[dofs(c), :] += a * A_c (D^-1 Ry)[dofs(c), :]      for every cell c     (dmode 1)
+// (dmode 2: the D^-1 scaling is applied to the output rows instead; dmode 0: none).
+//
+// Per (cell, column tile) work item: D (128 x BN, FP32 in TMEM) = A_c (128 x 128, cell matrix padded
+// from n_c <= 128) x X_c (128 x BN, the cell's rows of the block).  A persistent CTA per SM walks its
+// cells; for each cell it streams the column tiles.  Warp roles:
+//   warps 0-3  gather: thread k reads row dofs(c)[k] of R_Y (16-byte loads), scales by D^-1, rounds
+//              to the operand type and writes it transposed into the K-major 128-byte-swizzled
+//              shared-memory image of X_c (two stages), then fence.proxy.async + mbarrier arrive;
+//   warp 4     MMA issuer (one lane): tcgen05.mma kind::tf32 (K = 8) or kind::f16 (BF16, K = 16)
+//              into one of two TMEM accumulators, tcgen05.commit to release stages / buffers;
+//   warps 5-8  epilogue: tcgen05.ld of the accumulator rows (thread = cell-local dof), scaling, and
+//              vectorised float4 atomic scatter-add into R_X (dofs shared by neighbouring cells get
+//              one add per cell);
+//   warp 9     cell-matrix loader: one cp.async.bulk of the pre-swizzled cell-matrix image (two
+//              buffers, so the next cell's matrix streams in while the current one is in use).
+// The cell-matrix images are built once per operator and precision by a packing kernel.  Every
+// mbarrier wait is bounded; on a timeout the kernel raises the error flag and unwinds.
 #include "fe_tc.cuh"
+#include "prof.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+
 namespace rchfsi {
-void fe_tc_product(cudaStream_t, FeOp&, int, const float*, float*, int, float, int) {
-  throw Error(RCHFSI_ERR_UNSUPPORTED, "tensor-core FE product not built");
+namespace {
+
+constexpr int kNCP = 128;         // padded cell size (MMA M and K)
+constexpr int kThreads = 320;     // 10 warps
+constexpr int kRowBytes = 128;
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
+
+// Byte offset of element (row r, k) in a K-major 128B-swizzled image with `rows` rows per k-block.
+template <int ES>
+__device__ __forceinline__ uint32_t sw_off(int r, int k, int rows) {
+  constexpr int per = kRowBytes / ES;  // elements per 128-byte row
+  const int kb = k / per;
+  const int byte = (k % per) * ES;
+  const int chunk = (byte >> 4) ^ (r & 7);
+  return (uint32_t)kb * rows * kRowBytes + (uint32_t)r * kRowBytes + (chunk << 4) + (byte & 15);
+}
+
+// Pack cell matrices (n_cells x nc x nc, FP64, row-major) into per-cell 128 x 128 swizzled images.
+template <bool BF16>
+__global__ void pack_cells_kernel(int64_t n_cells, int nc, const double* __restrict__ A, uint8_t* __restrict__ img) {
+  constexpr int ES = BF16 ? 2 : 4;
+  const int64_t per_cell = (int64_t)kNCP * kNCP;
+  const int64_t total = n_cells * per_cell;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / per_cell;
+    const int r = (int)((e % per_cell) / kNCP), k = (int)(e % kNCP);
+    const double v = (r < nc && k < nc) ? A[(c * nc + r) * nc + k] : 0.0;
+    uint8_t* base = img + c * per_cell * ES + sw_off<ES>(r, k, kNCP);
+    if (BF16) *reinterpret_cast<__nv_bfloat16*>(base) = __float2bfloat16_rn((float)v);
+    else *reinterpret_cast<float*>(base) = tf32_rna((float)v);
+  }
+}
+
+struct FeArgs {
+  int64_t n_cells;
+  int nc, n, BN, ntiles;
+  uint32_t tmem_cols;
+  const int* dofs;
+  const uint8_t* img;   // packed cell images
+  const float* Ry;
+  float* Rx;
+  const double* dinv;
+  float a;
+  int dmode;
+  int* err;
+};
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <bool BF16, bool VEC>
+__global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(FeArgs p) {
+  constexpr int ES = BF16 ? 2 : 4;
+  constexpr int KMMA = BF16 ? 16 : 8;
+  constexpr uint32_t kFmt = BF16 ? 1u : 2u;
+  constexpr uint32_t kABytes = kNCP * kNCP * ES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[2], bempty[2], accfull[2], accempty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int BN = p.BN;
+  const uint32_t b_bytes = (uint32_t)BN * kNCP * ES;  // (128 / per) k-blocks x BN rows x 128 B
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA[2] = {smem, smem + kABytes};
+  uint8_t* sB[2] = {smem + 2 * kABytes, smem + 2 * kABytes + b_bytes};
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&afull[i], 1);
+      tc::mbar_init(&aempty[i], 1);
+      tc::mbar_init(&bfull[i], 128);
+      tc::mbar_init(&bempty[i], 1);
+      tc::mbar_init(&accfull[i], 1);
+      tc::mbar_init(&accempty[i], 128);
+    }
+    tc::fence_barrier_init();
+    abort_flag = 0;
+  }
+  if (warp == 4) {
+    tc::tmem_alloc(&tmem_slot, p.tmem_cols);
+    tc::tmem_relinquish();
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* vabort = &abort_flag;
+  auto fail = [&]() {
+    *vabort = 1;
+    atomicExch(p.err, 1);
+  };
+
+  const int64_t G = gridDim.x;
+  const int64_t my_cells = (p.n_cells > (int64_t)blockIdx.x) ? (p.n_cells - 1 - blockIdx.x) / G + 1 : 0;
+  const int64_t items = my_cells * p.ntiles;
+
+  if (warp < 4) {
+    // ---------------- gather: thread k owns cell-local dof k
+    const int k = threadIdx.x;
+    for (int64_t j = 0; j < items; ++j) {
+      const int64_t cl = j / p.ntiles;
+      const int t = (int)(j % p.ntiles);
+      const int64_t cell = blockIdx.x + cl * G;
+      const int bs = (int)(j & 1);
+      if (*vabort || !tc::mbar_wait(&bempty[bs], (uint32_t)((j >> 1) & 1) ^ 1u)) {
+        fail();
+        break;
+      }
+      uint8_t* img = sB[bs];
+      const int n0 = t * BN;
+      int g = -1;
+      float sc = 0.f;
+      if (k < p.nc) {
+        g = p.dofs[cell * p.nc + k];
+        sc = (p.dmode == 1) ? (float)p.dinv[g] : 1.f;
+      }
+      const float* row = (g >= 0) ? p.Ry + (int64_t)g * p.n : nullptr;
+      for (int nn = 0; nn < BN; nn += 4) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        const int col = n0 + nn;
+        if (row) {
+          if (VEC && col + 3 < p.n) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(row + col));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (col + u < p.n) v[u] = __ldg(row + col + u);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float x = v[u] * sc;
+          uint8_t* dst = img + sw_off<ES>(nn + u, k, BN);
+          if (BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(x);
+          else *reinterpret_cast<float*>(dst) = tf32_rna(x);
+        }
+      }
+      fence_proxy_async();
+      tc::mbar_arrive(&bfull[bs]);
+    }
+  } else if (warp == 4) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::instr_desc(kFmt, kNCP, BN);
+      for (int64_t j = 0; j < items; ++j) {
+        const int64_t cl = j / p.ntiles;
+        const int t = (int)(j % p.ntiles);
+        const int ab = (int)(cl & 1), bs = (int)(j & 1), xb = (int)(j & 1);
+        bool ok = !*vabort;
+        if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl >> 1) & 1));
+        if (ok) ok = tc::mbar_wait(&bfull[bs], (uint32_t)((j >> 1) & 1));
+        if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
+        if (!ok) {
+          fail();
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t a_base = tc::smem_u32(sA[ab]);
+        const uint32_t b_base = tc::smem_u32(sB[bs]);
+        const uint32_t d = tmem + (uint32_t)(xb * BN);
+        constexpr int per = kRowBytes / ES;
+#pragma unroll
+        for (int kk = 0; kk < kNCP / KMMA; ++kk) {
+          const int kel = kk * KMMA;
+          const uint32_t aoff = (uint32_t)(kel / per) * kNCP * kRowBytes + (uint32_t)((kel % per) * ES);
+          const uint32_t boff = (uint32_t)(kel / per) * BN * kRowBytes + (uint32_t)((kel % per) * ES);
+          const uint64_t ad = tc::sw128_desc(a_base + aoff);
+          const uint64_t bd = tc::sw128_desc(b_base + boff);
+          if (BF16) tc::mma_f16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          else tc::mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&bempty[bs]);
+        tc::mma_commit(&accfull[xb]);
+        if (t == p.ntiles - 1) tc::mma_commit(&aempty[ab]);
+      }
+    }
+  } else if (warp < 9) {
+    // ---------------- epilogue: TMEM -> scatter-add
+    const int q = warp & 3;
+    const int i = q * 32 + lane;  // cell-local dof of this thread's accumulator row
+    for (int64_t j = 0; j < items; ++j) {
+      const int64_t cl = j / p.ntiles;
+      const int t = (int)(j % p.ntiles);
+      const int64_t cell = blockIdx.x + cl * G;
+      const int xb = (int)(j & 1);
+      bool ok = !*vabort && tc::mbar_wait(&accfull[xb], (uint32_t)((j >> 1) & 1));
+      if (!ok) fail();
+      if (!__all_sync(0xffffffffu, ok && !*vabort)) break;
+      tc::tc_fence_after();
+      int g = -1;
+      float sc = 0.f;
+      if (i < p.nc) {
+        g = p.dofs[cell * p.nc + i];
+        sc = p.a * ((p.dmode == 2) ? (float)p.dinv[g] : 1.f);
+      }
+      float* out = (g >= 0) ? p.Rx + (int64_t)g * p.n : nullptr;
+      const int n0 = t * BN;
+      const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * BN);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(lane_addr + c0, v);
+        if (out) {
+#pragma unroll
+          for (int u = 0; u < 16; u += 4) {
+            const int col = n0 + c0 + u;
+            if (VEC && col + 3 < p.n) {
+              atomicAdd(reinterpret_cast<float4*>(out + col),
+                        make_float4(sc * v[u], sc * v[u + 1], sc * v[u + 2], sc * v[u + 3]));
+            } else {
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                if (col + w < p.n) atomicAdd(out + col + w, sc * v[u + w]);
+            }
+          }
+        }
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&accempty[xb]);
+    }
+  } else {
+    // ---------------- cell-matrix loader (warp 9, one lane)
+    if (lane == 0) {
+      int64_t issued = 0, cl = 0;
+      for (; cl < my_cells; ++cl) {
+        const int ab = (int)(cl & 1);
+        if (*vabort || !tc::mbar_wait(&aempty[ab], (uint32_t)((cl >> 1) & 1) ^ 1u)) {
+          fail();
+          break;
+        }
+        const int64_t cell = blockIdx.x + cl * G;
+        tc::mbar_arrive_expect_tx(&afull[ab], kABytes);
+        bulk_g2s(sA[ab], p.img + cell * (int64_t)kABytes, kABytes, &afull[ab]);
+        ++issued;
+      }
+      if (*vabort) {
+        // wait (bounded) for copies that may still be landing in this CTA's shared memory
+        for (int64_t c2 = (issued > 2 ? issued - 2 : 0); c2 < issued; ++c2)
+          tc::mbar_wait(&afull[c2 & 1], (uint32_t)((c2 >> 1) & 1));
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 4) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, p.tmem_cols);
+  }
+}
+
+}  // namespace
+
+void fe_tc_product(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a, int dmode) {
+  RC_CHECK(precision == RCHFSI_TF32 || precision == RCHFSI_BF16, RCHFSI_ERR_INVALID_ARG, "FE tensor path: TF32/BF16");
+  RC_CHECK(op.nc <= kNCP, RCHFSI_ERR_INVALID_ARG, "n_c larger than 128");
+  const bool bf = precision == RCHFSI_BF16;
+  const int ES = bf ? 2 : 4;
+  DevBuf<uint8_t>& img = bf ? op.img16 : op.imgtf;
+  const size_t per_cell = (size_t)kNCP * kNCP * ES;
+  if (!img.p) {
+    img.ensure(per_cell * op.n_cells);
+    const int64_t total = op.n_cells * (int64_t)kNCP * kNCP;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    if (bf) pack_cells_kernel<true><<<blocks, 256, 0, s>>>(op.n_cells, op.nc, op.A64.p, img.p);
+    else pack_cells_kernel<false><<<blocks, 256, 0, s>>>(op.n_cells, op.nc, op.A64.p, img.p);
+    RC_LAUNCH();
+  }
+  // column tile: widest multiple of 16 that keeps two matrix buffers + two operand stages in
+  // shared memory (227 KB) and two accumulators in TMEM (512 columns)
+  const int bn_max = bf ? 208 : 96;
+  const int ntiles = (n + bn_max - 1) / bn_max;
+  int BN = (((n + ntiles - 1) / ntiles) + 15) / 16 * 16;
+  if (BN < 16) BN = 16;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * BN)) cols <<= 1;
+  const size_t smem = 2 * per_cell + 2 * (size_t)BN * kNCP * ES + 1024;
+  RC_CHECK(smem <= 232448 - 1024, RCHFSI_ERR_INVALID_ARG, "FE tensor path: shared memory plan too large");
+  int dev = 0, sms = 152;
+  RC_CUDA(cudaGetDevice(&dev));
+  RC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  FeArgs p{op.n_cells, op.nc, n, BN, ntiles, cols, op.dofs.p, img.p, Ry, Rx, op.Dinv.p, a, dmode, op.err};
+  const bool vec = (n % 4) == 0;
+  auto kern = bf ? (vec ? fe_tc_kernel<true, true> : fe_tc_kernel<true, false>)
+                 : (vec ? fe_tc_kernel<false, true> : fe_tc_kernel<false, false>);
+  RC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(op.n_cells, (int64_t)sms);
+  const double nc = op.nc, C = (double)op.n_cells;
+  prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, 2.0 * nc * nc * C * n,
+                 4.0 * 3.0 * op.m * n + (double)ES * nc * nc * C);
+  kern<<<grid, kThreads, smem, s>>>(p);
+  RC_LAUNCH();
+}
+
 }  // namespace rchfsi

@@ -9,6 +9,7 @@
 //   store, the Chebyshev recurrence update (Algorithm 3 / Algorithm 2 loop body),
 //   reconstruction with a dense D^-1, or the residual W = AX - BX Lambda.
 #include "common.cuh"
+#include "prof.cuh"
 
 namespace rchfsi {
 namespace {
@@ -147,6 +148,9 @@ void gemm_dispatch(cudaStream_t s, int64_t M, int64_t N, int64_t K, const T* A, 
   RC_CHECK(cdiv(M, BM) <= 65535u, RCHFSI_ERR_INVALID_ARG, "gemm: M too large for the grid");
   dim3 grid(cdiv(N, BN), cdiv(M, BM));
   EpiDev<T> d = to_dev<T>(epi);
+  const double es = sizeof(T);
+  const double extra = (epi.kind == EPI_RECUR) ? (2.0 + (epi.Rx ? 1 : 0) + (epi.W ? 1 : 0)) : 1.0;
+  prof::Scope ps(s, epi.prof_cls, 2.0 * M * N * K, es * ((double)M * K + (double)K * N + extra * M * N));
   if (ak && bk) gemm_simt_kernel<T, true, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);
   else if (ak && !bk) gemm_simt_kernel<T, true, false><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);
   else if (!ak && bk) gemm_simt_kernel<T, false, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);

@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "fe.cuh"
+#include "prof.cuh"
 
 struct rchfsi_ctx;
 
@@ -62,6 +63,7 @@ struct rchfsi_ctx {
   double last_flops = 0.0;
   bool is_server = false;
   void* server = nullptr;
+  rchfsi::prof::Profiler prof;
 };
 
 namespace rchfsi {

@@ -20,6 +20,7 @@
 
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
+#include "prof.cuh"
 
 namespace rchfsi {
 namespace {
@@ -279,12 +280,21 @@ void run(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64_t K, const T* 
   float* ws = nullptr;
   if (p.nsplit > 1) ws = split.ensure((size_t)p.nsplit * M * N);
   dim3 grid(p.m_tiles, p.n_tiles, p.nsplit);
-  tc_gemm_kernel<T><<<grid, kThreads, p.smem, s>>>(ma, mb, (int)M, (int)N, (int)K, p.BN, p.tmem_cols,
-                                                    p.kb_per_split, ws, ep, err);
-  RC_LAUNCH();
+  const double es = sizeof(T);
+  const double epi_streams = 2.0 + (ep.Rx ? 1 : 0) + (ep.W ? 1 : 0);  // Ry, out, [Rx], [W]
+  {
+    // algorithmic bytes: A and R_Y once, plus the epilogue streams (direct) or the partials (split-K)
+    const double out_bytes = p.nsplit > 1 ? 4.0 * p.nsplit * M * N : epi_streams * es * M * N;
+    prof::Scope ps(s, RCHFSI_KERNEL_FILTER_TC, 2.0 * M * N * K, es * ((double)M * K + (double)K * N) + out_bytes);
+    tc_gemm_kernel<T><<<grid, kThreads, p.smem, s>>>(ma, mb, (int)M, (int)N, (int)K, p.BN, p.tmem_cols,
+                                                      p.kb_per_split, ws, ep, err);
+    RC_LAUNCH();
+  }
   if (p.nsplit > 1) {
     const int64_t total = M * N;
     int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+    prof::Scope ps(s, RCHFSI_KERNEL_SPLITK_REDUCE, (double)p.nsplit * M * N,
+                   4.0 * p.nsplit * M * N + epi_streams * es * M * N);
     splitk_reduce_kernel<T><<<(unsigned)blocks, 256, 0, s>>>((int)M, (int)N, p.nsplit, ws, ep);
     RC_LAUNCH();
   }
