@@ -261,6 +261,36 @@ int rchfsi_profile(struct rchfsi_ctx* h, int enable);
 int rchfsi_profile_read(struct rchfsi_ctx* h, int kernel_class, double* total_ms, int64_t* launches,
                         double* flops, double* bytes);
 
+/* ---------------------------------------------------------------- allocation-free filter step */
+
+/* Size of the fixed scratch array behind rchfsi_filter_step_tf32_static: 4 Mi floats (16 MiB). */
+#define RCHFSI_STATIC_SCRATCH_FLOATS (4u * 1024u * 1024u)
+
+/* One TF32 step of the filter recurrence that allocates no device memory.  The paper has no
+ * counterpart; it is for callers that cannot let a library call cudaMalloc -- for example a
+ * serving loop that must not allocate after start-up (cudaMalloc can synchronise the device and
+ * its latency is unbounded), or an application whose device memory is all owned by its own pool
+ * allocator.  The caller allocates and passes every input and output:
+ *   out = a * (A Ry) + b * Ry + c * Rx + a * W diag(lambda_y)
+ *   A        m x m FP32, row-major, row pitch lda (the operator A D^-1, values read as TF32)
+ *   Ry, Rx, W, out   m x n FP32, column-major, leading dimension ldr; Rx and W may be NULL (their
+ *            terms are dropped); out may alias Rx but not Ry or W
+ *   lambda_y n doubles
+ * lda and ldr must be >= m and multiples of 4; all arrays are device memory of the current device;
+ * cuda_stream is the stream to run on (NULL = legacy default stream).  Returns after the step has
+ * completed (the stream is synchronised).
+ * Scratch: the split-K partial sums live in one file-scope __device__ array of
+ * RCHFSI_STATIC_SCRATCH_FLOATS floats, which every GPU that loads the library holds until the
+ * process exits.  Shapes whose partials need more return RCHFSI_ERR_INVALID_ARG with a message
+ * giving both sizes (rchfsi_last_error(NULL, ...)).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and its timeout flag: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG (sizes, pitches, host pointers, scratch too small), TIMEOUT, CUDA. */
+int rchfsi_filter_step_tf32_static(const float* A, int64_t lda, const float* Ry, const float* Rx, const float* W,
+                                   const double* lambda_y, float a, float b, float c, int64_t m, int64_t n,
+                                   int64_t ldr, float* out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- errors */
 const char* rchfsi_strerror(int code);
 /* Copy the last error message of the handle (NUL-terminated, truncated to len). */

@@ -90,6 +90,9 @@ SIGNATURES = {
     "rchfsi_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rchfsi_result)]),
     "rchfsi_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rchfsi_profile_read": (C.c_int, [C.c_void_p, C.c_int, dptr, C.POINTER(C.c_int64), dptr, dptr]),
+    "rchfsi_filter_step_tf32_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                 C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_int64,
+                                                 C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),
     "rchfsi_strerror": (C.c_char_p, [C.c_int]),
     "rchfsi_last_error": (C.c_int, [C.c_void_p, C.c_char_p, C.c_size_t]),
 }

@@ -31,6 +31,15 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+namespace rchfsi {
+// Message returned by rchfsi_last_error(NULL, ...) on this thread.
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace rchfsi
+
+namespace {
+
 struct ProfBind {
   prof::Profiler* prev;
   explicit ProfBind(rchfsi_ctx* h) : prev(prof::current()) { prof::current() = h ? &h->prof : nullptr; }

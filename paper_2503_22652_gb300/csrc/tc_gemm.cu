@@ -315,4 +315,37 @@ void tc_gemm_bf16_recur(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64
   run<__nv_bfloat16>(s, num_sms, M, N, K, A, lda, B, ldb, split, e, err);
 }
 
+size_t tc_gemm_tf32_split_floats(int num_sms, int64_t M, int64_t N, int64_t K) {
+  const Plan p = make_plan(num_sms, M, N, K, kRowBytes / 4);
+  return p.nsplit > 1 ? (size_t)p.nsplit * M * N : 0;
+}
+
+void tc_gemm_tf32_recur_ws(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                           const float* B, int64_t ldb, float* ws, size_t ws_floats, const TcRecur& r, int64_t ldo,
+                           int* err) {
+  // The launch sequence of run<float>() with caller-provided storage for the split-K partials.
+  constexpr int BK = kRowBytes / 4;
+  RC_CHECK(M > 0 && N > 0 && K > 0, RCHFSI_ERR_INVALID_ARG, "tensor-core GEMM with an empty dimension");
+  RC_CHECK(M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31), RCHFSI_ERR_INVALID_ARG, "GEMM too large");
+  const Plan p = make_plan(num_sms, M, N, K, BK);
+  RC_CHECK(p.nsplit == 1 || (size_t)p.nsplit * M * N <= ws_floats, RCHFSI_ERR_INVALID_ARG,
+           "split-K partials need " + std::to_string((size_t)p.nsplit * M * N) + " floats, scratch holds " +
+               std::to_string(ws_floats));
+  const CUtensorMap ma = make_map(A, false, K, M, lda, kBM);
+  const CUtensorMap mb = make_map(B, false, K, N, ldb, p.BN);
+  RC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 4096));
+  Epi<float> ep{r.a, r.b, r.c, r.Ry, r.Rx, r.W, r.lam, r.out, ldo};
+  float* w = p.nsplit > 1 ? ws : nullptr;
+  dim3 grid(p.m_tiles, p.n_tiles, p.nsplit);
+  tc_gemm_kernel<float><<<grid, kThreads, p.smem, s>>>(ma, mb, (int)M, (int)N, (int)K, p.BN, p.tmem_cols,
+                                                        p.kb_per_split, w, ep, err);
+  RC_LAUNCH();
+  if (p.nsplit > 1) {
+    const int64_t total = M * N;
+    int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+    splitk_reduce_kernel<float><<<(unsigned)blocks, 256, 0, s>>>((int)M, (int)N, p.nsplit, w, ep);
+    RC_LAUNCH();
+  }
+}
+
 }  // namespace rchfsi

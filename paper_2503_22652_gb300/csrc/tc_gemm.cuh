@@ -34,4 +34,13 @@ void tc_gemm_bf16_recur(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64
                         int64_t lda, const __nv_bfloat16* B, int64_t ldb, DevBuf<float>& split, const TcRecur16& r,
                         int64_t ldo, int* err);
 
+// Floats of split-K partial sums the TF32 GEMM plan needs for this shape (0 when it does not split).
+size_t tc_gemm_tf32_split_floats(int num_sms, int64_t M, int64_t N, int64_t K);
+
+// tc_gemm_tf32_recur with caller-provided split-K storage (ws, ws_floats) instead of a DevBuf:
+// allocates nothing.  Throws INVALID_ARG when the plan needs more than ws_floats.
+void tc_gemm_tf32_recur_ws(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                           const float* B, int64_t ldb, float* ws, size_t ws_floats, const TcRecur& r, int64_t ldo,
+                           int* err);
+
 }  // namespace rchfsi
