@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default="dense", choices=["dense", "fe"])
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed solves only: no comparisons, no end-to-end run, no CPU baseline (profiling runs)")
     return ap.parse_args()
 
 
@@ -326,9 +328,9 @@ def run_gpu(args, rank, world, local_rank):
     pk = peaks()
     kname, roof = roofline(prof, sum(times), pk, args.precision)
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not (args.no_extras or args.quick) and rank == 0:
         extras = comparisons(s, prob, args, torch, dev, stream)
-    e2e = end_to_end(prob, args, torch) if rank == 0 else None
+    e2e = end_to_end(prob, args, torch) if rank == 0 and not args.quick else None
     if rank != 0:
         return None
     sorted_t = sorted(times)
@@ -350,7 +352,9 @@ def run_gpu(args, rank, world, local_rank):
            "kernel_classes_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e}
     out.update(extras)
-    out["cpu_baseline"] = cpu_baseline(prob, iters[-1])
+    out["cpu_baseline"] = None if args.quick else cpu_baseline(prob, iters[-1])
+    rr_other = st_last["t_rr_ms"] - (prof["gemm_f64"]["ms"] + prof["fe_cell_f64"]["ms"]) / args.steps
+    out["rr_non_gemm_ms"] = round(rr_other, 3)
     return out
 
 

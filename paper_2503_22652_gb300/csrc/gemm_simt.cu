@@ -1,13 +1,18 @@
 // SIMT (FFMA / DFMA) tiled GEMM with fused epilogues.
 //
 // FP64 work on this GPU is bound by the FP64 ALUs (about 1.1 TFLOP/s for the whole chip, 1/64 of
-// the FP32 FFMA rate), so a register-tiled SIMT kernel reaches the FP64 roofline; the same code in
-// FP32 is the "FP32 arithmetic" filter path of the paper (products in FP32 on the FFMA pipes).
+// the FP32 FFMA rate), so a register-tiled SIMT kernel is the FP64 path; the same code in FP32 is
+// the "FP32 arithmetic" filter path of the paper (products in FP32 on the FFMA pipes).
 //
 // Tile: 64 x 64 outputs per CTA, K step 16, 256 threads, 4 x 4 outputs per thread at stride 16
 // (conflict-free shared-memory reads).  The epilogue applies one of:
 //   store, the Chebyshev recurrence update (Algorithm 3 / Algorithm 2 loop body),
 //   reconstruction with a dense D^-1, or the residual W = AX - BX Lambda.
+// Shapes with few output tiles and a long K (the N x N Gram matrices Y^T A Y, Y^T B Y) are split
+// along K across CTAs so that every SM works: each split writes its partial tile to a workspace and
+// a second kernel sums the partials in a fixed order (deterministic) and applies the epilogue.
+#include <algorithm>
+
 #include "common.cuh"
 #include "prof.cuh"
 
@@ -57,23 +62,27 @@ struct EpiDev {
   }
 };
 
+// blockIdx.z selects the K slice [z*kslice, min(K, (z+1)*kslice)); with `partial` set the raw
+// accumulators go to partial[z][j*M + i] instead of through the epilogue.
 template <typename T, bool AK, bool BKC>
 __global__ void __launch_bounds__(NT) gemm_simt_kernel(int64_t M, int64_t N, int64_t K, const T* __restrict__ A,
                                                        int64_t lda, const T* __restrict__ B, int64_t ldb,
-                                                       EpiDev<T> epi) {
+                                                       EpiDev<T> epi, int64_t kslice, T* __restrict__ partial) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int64_t i0 = (int64_t)blockIdx.y * BM;
   const int64_t j0 = (int64_t)blockIdx.x * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * kslice;
+  const int64_t kend = min(K, kbeg + kslice);
   T acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
 
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < (BM * BK) / NT; ++q) {
       const int e = tid + q * NT;
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int64_t M, int64_t N, int
       if (AK) { kk = e % BK; ii = e / BK; } else { ii = e % BM; kk = e / BM; }
       const int64_t gi = i0 + ii, gk = k0 + kk;
       T v = T(0);
-      if (gi < M && gk < K) v = AK ? A[gi * lda + gk] : A[gk * lda + gi];
+      if (gi < M && gk < kend) v = AK ? A[gi * lda + gk] : A[gk * lda + gi];
       As[kk][ii] = v;
     }
 #pragma unroll
@@ -91,7 +100,7 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int64_t M, int64_t N, int
       if (BKC) { kk = e % BK; jj = e / BK; } else { jj = e % BN; kk = e / BN; }
       const int64_t gj = j0 + jj, gk = k0 + kk;
       T v = T(0);
-      if (gj < N && gk < K) v = BKC ? B[gj * ldb + gk] : B[gk * ldb + gj];
+      if (gj < N && gk < kend) v = BKC ? B[gj * ldb + gk] : B[gk * ldb + gj];
       Bs[kk][jj] = v;
     }
     __syncthreads();
@@ -116,8 +125,22 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int64_t M, int64_t N, int
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t gj = j0 + tx + 16 * q;
-      if (gj < N) epi(gi, gj, acc[r][q]);
+      if (gj < N) {
+        if (partial) partial[((int64_t)blockIdx.z * N + gj) * M + gi] = acc[r][q];
+        else epi(gi, gj, acc[r][q]);
+      }
     }
+  }
+}
+
+template <typename T>
+__global__ void splitk_sum_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ partial, EpiDev<T> epi) {
+  const int64_t total = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / M, i = e - j * M;
+    T acc = T(0);
+    for (int s = 0; s < nsplit; ++s) acc += partial[(int64_t)s * total + e];
+    epi(i, j, acc);
   }
 }
 
@@ -141,21 +164,49 @@ EpiDev<T> to_dev(const EpiArgs& e) {
   return d;
 }
 
+// Per-host-thread workspace of split-K partials (calls of one thread run in stream order).
+template <typename T>
+DevBuf<T>& split_ws() {
+  static thread_local DevBuf<T> ws;
+  return ws;
+}
+
 template <typename T>
 void gemm_dispatch(cudaStream_t s, int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, bool ak, const T* B,
                    int64_t ldb, bool bk, const EpiArgs& epi) {
   if (M <= 0 || N <= 0) return;
   RC_CHECK(cdiv(M, BM) <= 65535u, RCHFSI_ERR_INVALID_ARG, "gemm: M too large for the grid");
-  dim3 grid(cdiv(N, BN), cdiv(M, BM));
+  const int64_t tiles = (int64_t)cdiv(N, BN) * cdiv(M, BM);
+  // split K when the output alone cannot fill the GPU (target ~4 CTAs per SM, slices >= 256)
+  int nsplit = 1;
+  const int64_t want = 152 * 4;
+  if (tiles < want && K >= 512) {
+    nsplit = (int)std::min<int64_t>((want + tiles - 1) / tiles, K / 256);
+    nsplit = std::max(nsplit, 1);
+    nsplit = std::min(nsplit, 64);
+  }
+  int64_t kslice = (K + nsplit - 1) / nsplit;
+  kslice = (kslice + BK - 1) / BK * BK;
+  nsplit = (int)((K + kslice - 1) / kslice);
+  if (nsplit < 1) nsplit = 1;
+  T* part = nullptr;
+  if (nsplit > 1) part = split_ws<T>().ensure((size_t)nsplit * M * N);
+  dim3 grid(cdiv(N, BN), cdiv(M, BM), nsplit);
   EpiDev<T> d = to_dev<T>(epi);
   const double es = sizeof(T);
   const double extra = (epi.kind == EPI_RECUR) ? (2.0 + (epi.Rx ? 1 : 0) + (epi.W ? 1 : 0)) : 1.0;
   prof::Scope ps(s, epi.prof_cls, 2.0 * M * N * K, es * ((double)M * K + (double)K * N + extra * M * N));
-  if (ak && bk) gemm_simt_kernel<T, true, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);
-  else if (ak && !bk) gemm_simt_kernel<T, true, false><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);
-  else if (!ak && bk) gemm_simt_kernel<T, false, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);
-  else gemm_simt_kernel<T, false, false><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d);
+  if (ak && bk) gemm_simt_kernel<T, true, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d, kslice, part);
+  else if (ak && !bk) gemm_simt_kernel<T, true, false><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d, kslice, part);
+  else if (!ak && bk) gemm_simt_kernel<T, false, true><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d, kslice, part);
+  else gemm_simt_kernel<T, false, false><<<grid, NT, 0, s>>>(M, N, K, A, lda, B, ldb, d, kslice, part);
   RC_LAUNCH();
+  if (nsplit > 1) {
+    const int64_t total = M * N;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    splitk_sum_kernel<T><<<blocks, 256, 0, s>>>(M, N, nsplit, part, d);
+    RC_LAUNCH();
+  }
 }
 
 }  // namespace
