@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default="dense", choices=["dense", "fe"])
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
+    ap.add_argument("--rr", default="emulated", choices=["fp64", "emulated"],
+                    help="FP64 products of residual / Rayleigh-Ritz: DFMA or BF16-slice emulation")
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only: no comparisons, no end-to-end run, no CPU baseline (profiling runs)")
     return ap.parse_args()
@@ -248,6 +250,14 @@ def roofline(prof, solve_ms_total, pk, precision):
                       "peak_source": "measured bf16 sustained x nominal %s/bf16 ratio %.2f (of measured)" % (
                           precision, ratio),
                       "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
+    if name == "gemm_f64_emu":
+        # the 28 BF16 slice products per FP64-accurate product run on the tensor cores
+        ach = r["flops"] / (r["ms"] * 1e-3) / 1e12
+        return name, {"bound": "tensor", "achieved": round(ach, 2), "peak": round(bf16, 1), "unit": "TFLOP/s",
+                      "frac": round(ach / bf16, 4), "traffic": None,
+                      "peak_source": "measured bf16 sustained (of measured)",
+                      "fp64_equivalent_tflops": round(ach / 28.0, 2),
+                      "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
     if name in ("gemm_f64", "filter_simt"):
         ach = r["flops"] / (r["ms"] * 1e-3) / 1e12
         peak = 1.25 if name == "gemm_f64" else 69.8
@@ -277,7 +287,7 @@ def run_gpu(args, rank, world, local_rank):
     m, N = prob["m"], prob["block"]
     stream = torch.cuda.current_stream()
     s = Solver(m, nev=prob["nev"], block=N, degree=prob["degree"], precision=args.precision, max_iter=200,
-               tol=prob["tol"], stream=stream.cuda_stream)
+               tol=prob["tol"], stream=stream.cuda_stream, rr_mode=args.rr)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     if "dense" in prob:
         c = prob["dense"]
@@ -314,7 +324,7 @@ def run_gpu(args, rank, world, local_rank):
         iters.append(st["iterations"])
         resid.append(st["max_rel_residual"])
     prof = {k: s.profile_read(k) for k in ("filter_tc", "splitk_reduce", "filter_simt", "gemm_f64", "fe_cell",
-                                           "fe_cell_f64")}
+                                           "fe_cell_f64", "gemm_f64_emu")}
     launches = s.profile_read("all")["launches"]
     s.profile(False)
     clocks = clk.stop()
@@ -353,7 +363,9 @@ def run_gpu(args, rank, world, local_rank):
            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e}
     out.update(extras)
     out["cpu_baseline"] = None if args.quick else cpu_baseline(prob, iters[-1])
-    rr_other = st_last["t_rr_ms"] - (prof["gemm_f64"]["ms"] + prof["fe_cell_f64"]["ms"]) / args.steps
+    rr_other = st_last["t_rr_ms"] - (prof["gemm_f64"]["ms"] + prof["fe_cell_f64"]["ms"] +
+                                     prof["gemm_f64_emu"]["ms"]) / args.steps
+    out["config"]["rr_products"] = args.rr
     out["rr_non_gemm_ms"] = round(rr_other, 3)
     return out
 
@@ -411,7 +423,7 @@ def end_to_end(prob, args, torch):
         return t.numpy()
 
     s = Solver(m, nev=prob["nev"], block=N, degree=prob["degree"], precision=args.precision, max_iter=200,
-               tol=prob["tol"])
+               tol=prob["tol"], rr_mode=args.rr)
     if "dense" in prob:
         c = prob["dense"]
         args_op = dict(A=pinned(c["A"]), B=pinned(c["B"]), Dinv=pinned(c["Dinv"]))

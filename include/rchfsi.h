@@ -86,7 +86,16 @@ typedef struct rchfsi_params {
   double tol;            /* relative residual tolerance ||Ax - eps Bx|| / (||A|| ||x||) */
   double lmin, lT, lmax; /* bounds when fixed_bounds = 1 */
   uint64_t hbm_budget_bytes; /* device memory the handle may hold (0 = unlimited) */
+  int32_t rr_mode;       /* FP64 products of the residual / Rayleigh-Ritz steps: RCHFSI_RR_FP64 (FP64
+                            arithmetic units) or RCHFSI_RR_FP64_EMULATED (FP64-accurate products from
+                            exact BF16 slices on the tensor cores) */
+  int32_t reserved0;
 } rchfsi_params;
+
+typedef enum {
+  RCHFSI_RR_FP64 = 0,          /* FP64 FMA (DFMA) GEMMs */
+  RCHFSI_RR_FP64_EMULATED = 1  /* error-free BF16 splitting, 7 slices, exact per-chunk FP32 sums */
+} rchfsi_rr_mode;
 
 /* Operator description for rchfsi_set_operator.  Unused fields must be 0 / NULL.
  * Dense:  A (m*m, row-major, symmetric), optional B (m*m; NULL = identity), optional A_filter
@@ -135,7 +144,8 @@ typedef struct rchfsi_stats {
 /* ---------------------------------------------------------------- lifecycle */
 
 /* Fill *p with defaults: nev = 1, block = 1, degree = 20, FP64, R-ChFSI, real, max_iter = 100,
- * min_iter = 0, lanczos_steps = 10, stall_iters = 0, fixed_bounds = 0, tol = 1e-8. */
+ * min_iter = 0, lanczos_steps = 10, stall_iters = 0, fixed_bounds = 0, tol = 1e-8,
+ * rr_mode = RCHFSI_RR_FP64. */
 int rchfsi_params_default(rchfsi_params* p);
 
 /* Create a handle on the current CUDA device.  cuda_stream: a cudaStream_t to run on, or NULL
@@ -247,7 +257,9 @@ typedef enum {
   RCHFSI_KERNEL_GEMM_F64 = 3,      /* FP64 GEMMs of the residual and Rayleigh-Ritz steps */
   RCHFSI_KERNEL_FE_CELL = 4,       /* FE cell-matrix product inside the filter */
   RCHFSI_KERNEL_FE_CELL_F64 = 5,   /* FE cell-matrix product of the residual / Rayleigh-Ritz (FP64) */
-  RCHFSI_KERNEL_CLASSES = 6
+  RCHFSI_KERNEL_GEMM_F64_EMU = 6,  /* FP64-accurate GEMM from BF16 slices on the tensor cores; flops are
+                                      the tensor-core flops (28 slice products) */
+  RCHFSI_KERNEL_CLASSES = 7
 } rchfsi_kernel_class;
 
 /* enable = 1: start timing every instrumented launch of this handle with CUDA events on the

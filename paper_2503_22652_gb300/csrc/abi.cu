@@ -82,6 +82,8 @@ void validate_params(const rchfsi_params* p) {
            "lanczos_steps must be in [2, m]");
   RC_CHECK(p->tol >= 0.0, RCHFSI_ERR_INVALID_ARG, "tol must be >= 0");
   RC_CHECK(p->block <= 6144, RCHFSI_ERR_UNSUPPORTED, "block larger than 6144");
+  RC_CHECK(p->rr_mode == RCHFSI_RR_FP64 || p->rr_mode == RCHFSI_RR_FP64_EMULATED, RCHFSI_ERR_INVALID_ARG,
+           "bad rr_mode");
 }
 
 void need_op(rchfsi_ctx* h) {
@@ -146,6 +148,8 @@ void set_dense(rchfsi_ctx& c, const rchfsi_operator* op) {
   RC_CHECK(op->A, RCHFSI_ERR_INVALID_ARG, "dense operator needs A");
   RC_CHECK(!(op->Dinv && op->Dinv_dense), RCHFSI_ERR_INVALID_ARG, "give Dinv or Dinv_dense, not both");
   d.AD32.release(); d.DA32.release(); d.ADtf.release(); d.DAtf.release(); d.AD16.release(); d.DA16.release();
+  d.ozA.R = 0;  // slices of the previous operator are stale
+  d.ozB.R = 0;
   to_device(c, op->A, d.A.ensure(mm), mm);
   d.has_B = op->B != nullptr;
   if (d.has_B) to_device(c, op->B, d.B.ensure(mm), mm);

@@ -475,11 +475,37 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   }
   double* AY = w.AY.p;
   double* BY = w.BY.p;
-  apply_A_f64(c, Y, AY, N);
-  apply_B_f64(c, Y, BY, N);
-  // G_A = Y^T A Y, G_B = Y^T B Y  (N x N, column-major)
-  gemm_f64(c.s, N, N, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
-  gemm_f64(c.s, N, N, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
+  const bool emu = c.p.rr_mode == RCHFSI_RR_FP64_EMULATED;
+  int* eflag = w.info.p + 2;
+  if (emu) {
+    // FP64-accurate products from BF16 slices: Y as N logical rows of length m
+    oz_slice(c.s, N, m, Y, m, 1, w.ozL);
+    if (c.op_kind == RCHFSI_OP_DENSE) {
+      DenseOp& d = c.dense;
+      if (d.ozA.R != m) oz_slice(c.s, m, m, d.A.p, m, 1, d.ozA);
+      oz_gemm(c.s, c.num_sms, d.ozA, w.ozL, AY, m, w.ozws, eflag);
+      if (d.has_B) {
+        if (d.ozB.R != m) oz_slice(c.s, m, m, d.B.p, m, 1, d.ozB);
+        oz_gemm(c.s, c.num_sms, d.ozB, w.ozL, BY, m, w.ozws, eflag);
+      } else {
+        RC_CUDA(cudaMemcpyAsync(BY, Y, sizeof(double) * m * N, cudaMemcpyDeviceToDevice, c.s));
+      }
+    } else {
+      apply_A_f64(c, Y, AY, N);
+      apply_B_f64(c, Y, BY, N);
+    }
+    // G_A = Y^T A Y, G_B = Y^T B Y
+    oz_slice(c.s, N, m, AY, m, 1, w.ozR);
+    oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GA.p, N, w.ozws, eflag);
+    oz_slice(c.s, N, m, BY, m, 1, w.ozR);
+    oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag);
+  } else {
+    apply_A_f64(c, Y, AY, N);
+    apply_B_f64(c, Y, BY, N);
+    // G_A = Y^T A Y, G_B = Y^T B Y  (N x N, column-major)
+    gemm_f64(c.s, N, N, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
+    gemm_f64(c.s, N, N, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
+  }
   symmetrize_f64(c.s, N, w.GA.p, N);
   symmetrize_f64(c.s, N, w.GB.p, N);
   cholesky_f64(c.s, N, w.GB.p, N, w.info.p);
@@ -496,9 +522,27 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   // E = L^-T V
   trsm_lower_trans_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
   // X = Y E, AX = AY E, BX = BY E
-  gemm_f64(c.s, m, N, N, Y, m, false, w.Z.p, N, true, epi_store(X, m));
-  gemm_f64(c.s, m, N, N, AY, m, false, w.Z.p, N, true, epi_store(AX, m));
-  gemm_f64(c.s, m, N, N, BY, m, false, w.Z.p, N, true, epi_store(BX, m));
+  if (emu) {
+    // E^T as N logical rows (row j = column j of E, contiguous); blocks as m logical rows (dofs)
+    oz_slice(c.s, N, N, w.Z.p, N, 1, w.ozE);
+    oz_slice(c.s, m, N, Y, 1, m, w.ozL);
+    oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, X, m, w.ozws, eflag);
+    oz_slice(c.s, m, N, AY, 1, m, w.ozL);
+    oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, AX, m, w.ozws, eflag);
+    oz_slice(c.s, m, N, BY, 1, m, w.ozL);
+    oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, BX, m, w.ozws, eflag);
+    int flag = 0;
+    RC_CUDA(cudaMemcpyAsync(&flag, eflag, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    if (flag) {
+      RC_CUDA(cudaMemsetAsync(eflag, 0, sizeof(int), c.s));
+      throw Error(RCHFSI_ERR_TIMEOUT, "a bounded wait in the emulated FP64 GEMM ran out");
+    }
+  } else {
+    gemm_f64(c.s, m, N, N, Y, m, false, w.Z.p, N, true, epi_store(X, m));
+    gemm_f64(c.s, m, N, N, AY, m, false, w.Z.p, N, true, epi_store(AX, m));
+    gemm_f64(c.s, m, N, N, BY, m, false, w.Z.p, N, true, epi_store(BX, m));
+  }
   RC_CUDA(cudaMemcpyAsync(&info, w.info.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaStreamSynchronize(c.s));
   if (info != 0) return RCHFSI_ERR_NUMERIC;

@@ -1,0 +1,400 @@
+// FP64-accurate products from BF16 tensor-core slices (see oz_gemm.cuh for the scheme).
+//
+// oz_gemm_kernel: one CTA per 128 x 32 output tile and K range.  Warp 0 (one lane) streams, per
+// 64-wide K chunk, the 7 B slices of the tile (one 28 KB stage, two stages) and the 7 A slices
+// (16 KB each, a 6-deep ring) with TMA; warp 1 (one lane) issues, for each A slice s, the products
+// with B slices t <= 6 - s (4 x tcgen05.mma kind::f16, K = 16) into the TMEM accumulator of level
+// s + t (7 levels x 32 columns, two buffers = 448 columns); warps 4-11 (two per TMEM lane quarter,
+// 16 columns each) drain a finished chunk: tcgen05.ld of the 7 levels, exact scaling by 2^-8L and
+// TwoSum into per-output float-float accumulators.  The final value (hi + lo) 2^(e_i + f_j - 16) is
+// stored in FP64 (or, with split-K, written as a partial and summed by a second kernel).
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "oz_gemm.cuh"
+#include "prof.cuh"
+#include "tc_ptx.cuh"
+
+namespace rchfsi {
+namespace {
+
+constexpr int S = kOzSlices;
+constexpr int BM = 128;
+constexpr int BN = 32;
+constexpr int KC = 64;            // K chunk: one 128-byte row of BF16
+constexpr int ASTAGES = 6;
+constexpr int kThreads = 384;     // 12 warps
+constexpr uint32_t kABytes = BM * 128;       // 16 KB per A slice tile
+constexpr uint32_t kBBytes = S * BN * 128;   // 28 KB: all B slices of one chunk
+constexpr uint32_t kTmemCols = 512;          // 2 buffers x 7 levels x 32 columns = 448
+
+// ---------------------------------------------------------------- slicing
+__device__ __forceinline__ int exp_of(double x) {
+  int e = 0;
+  if (x != 0.0) frexp(x, &e);
+  return x != 0.0 ? e : -100000;
+}
+
+// Row exponents, K-contiguous rows: one warp per row.
+__global__ void rowexp_kcontig(int64_t R, int64_t K, const double* __restrict__ X, int64_t rs, int* ex) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= R) return;
+  int e = -100000;
+  for (int64_t k = lane; k < K; k += 32) e = max(e, exp_of(X[r * rs + k]));
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) ex[r] = (e == -100000) ? 0 : e;
+}
+
+// Row exponents, rows contiguous across threads (element (r, k) at X[r + k * ks]): thread per row.
+__global__ void rowexp_rcontig(int64_t R, int64_t K, const double* __restrict__ X, int64_t ks, int* ex) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  int e = -100000;
+  for (int64_t k = 0; k < K; ++k) e = max(e, exp_of(X[r + k * ks]));
+  ex[r] = (e == -100000) ? 0 : e;
+}
+
+// Slices of a 32-row x 64-k tile.  Block (32, 8).
+__global__ void slice_kernel(int64_t R, int64_t Rp, int64_t K, int64_t Kp, const double* __restrict__ X, int64_t rs,
+                             int64_t ks, const int* __restrict__ ex, __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[32][KC + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * KC;
+  if (ks == 1) {
+    for (int rr = ty; rr < 32; rr += 8)
+      for (int kk = tx; kk < KC; kk += 32) {
+        const int64_t r = r0 + rr, k = k0 + kk;
+        tile[rr][kk] = (r < R && k < K) ? X[r * rs + k] : 0.0;
+      }
+  } else {
+    for (int kk = ty; kk < KC; kk += 8) {
+      const int64_t r = r0 + tx, k = k0 + kk;
+      tile[tx][kk] = (r < R && k < K) ? X[r * rs + k * ks] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t r = r0 + rr;
+    if (r >= R) continue;
+    const int e = ex[r];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int kk = 2 * tx + h;
+      double v = ldexp(tile[rr][kk], -e);
+      for (int s = 0; s < S; ++s) {
+        const double t = rint(v * 256.0);
+        v = v * 256.0 - t;
+        out[((int64_t)s * Rp + r) * Kp + k0 + kk] = __float2bfloat16_rn((float)t);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- the product
+struct OzArgs {
+  int M, N;
+  int MP, NP;      // rows per slice in the A and B slice tensors
+  int chunks_per_split, nchunks;
+  const int* ea;
+  const int* eb;
+  double* C;       // final output (nsplit == 1) or partials [split][N][M]
+  int64_t ldc;
+  int partial;
+  int* err;
+};
+
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += e;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t afull[ASTAGES], aempty[ASTAGES], bfull[2], bempty[2], accfull[2], accempty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, split = blockIdx.z;
+  const int c_begin = split * p.chunks_per_split;
+  const int nch = min(p.nchunks, c_begin + p.chunks_per_split) - c_begin;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;                                  // ASTAGES x 16 KB
+  uint8_t* sB = smem + (size_t)ASTAGES * kABytes;      // 2 x 28 KB
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ASTAGES; ++i) {
+      tc::mbar_init(&afull[i], 1);
+      tc::mbar_init(&aempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&bfull[i], 1);
+      tc::mbar_init(&bempty[i], 1);
+      tc::mbar_init(&accfull[i], 1);
+      tc::mbar_init(&accempty[i], 256);
+    }
+    tc::fence_barrier_init();
+    abort_flag = 0;
+    tc::prefetch_tmap(&mapA);
+    tc::prefetch_tmap(&mapB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&tmem_slot, kTmemCols);
+    tc::tmem_relinquish();
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* vabort = &abort_flag;
+  auto fail = [&]() {
+    *vabort = 1;
+    atomicExch(p.err, 1);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      for (int ci = 0; ci < nch; ++ci) {
+        const int k0 = (c_begin + ci) * KC;
+        const int b = ci & 1;
+        if (*vabort || !tc::mbar_wait(&bempty[b], (uint32_t)((ci >> 1) & 1) ^ 1u)) {
+          fail();
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&bfull[b], kBBytes);
+        for (int t = 0; t < S; ++t)
+          tc::tma_load_2d(sB + (size_t)b * kBBytes + (size_t)t * BN * 128, &mapB, &bfull[b], k0, t * p.NP + n0);
+        bool ok = true;
+        for (int s = 0; s < S; ++s) {
+          const int j = ci * S + s;
+          const int q = j % ASTAGES;
+          if (*vabort || !tc::mbar_wait(&aempty[q], (uint32_t)((j / ASTAGES) & 1) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&afull[q], kABytes);
+          tc::tma_load_2d(sA + (size_t)q * kABytes, &mapA, &afull[q], k0, s * p.MP + m0);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = tc::instr_desc(1u, BM, BN);  // BF16 x BF16 -> FP32, M = 128, N = 32
+      for (int ci = 0; ci < nch; ++ci) {
+        const int b = ci & 1;
+        bool ok = !*vabort && tc::mbar_wait(&bfull[b], (uint32_t)((ci >> 1) & 1));
+        if (ok) ok = tc::mbar_wait(&accempty[b], (uint32_t)((ci >> 1) & 1) ^ 1u);
+        if (!ok) {
+          fail();
+          break;
+        }
+        const uint32_t b_base = tc::smem_u32(sB + (size_t)b * kBBytes);
+        const uint32_t d_base = tmem + (uint32_t)(b * S * BN);
+        for (int s = 0; s < S; ++s) {
+          const int j = ci * S + s;
+          const int q = j % ASTAGES;
+          if (*vabort || !tc::mbar_wait(&afull[q], (uint32_t)((j / ASTAGES) & 1))) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a_base = tc::smem_u32(sA + (size_t)q * kABytes);
+          for (int t = 0; t + s < S; ++t) {
+            const uint32_t d = d_base + (uint32_t)((s + t) * BN);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = tc::sw128_desc(a_base + kk * 32);
+              const uint64_t bd = tc::sw128_desc(b_base + (uint32_t)(t * BN * 128) + kk * 32);
+              tc::mma_f16(d, ad, bd, idesc, (s == 0 && kk == 0) ? 0u : 1u);
+            }
+          }
+          tc::mma_commit(&aempty[q]);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        tc::mma_commit(&bempty[b]);
+        tc::mma_commit(&accfull[b]);
+      }
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue: 8 warps, lane quarter q, column half h
+    const int q = warp & 3, h = (warp - 4) >> 2;
+    float hi[16], lo[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) hi[u] = lo[u] = 0.f;
+    bool ok = true;
+    for (int ci = 0; ci < nch; ++ci) {
+      const int b = ci & 1;
+      bool w = !*vabort && tc::mbar_wait(&accfull[b], (uint32_t)((ci >> 1) & 1));
+      if (!w) fail();
+      if (!__all_sync(0xffffffffu, w && !*vabort)) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * S * BN + h * 16);
+      float scale = 1.f;
+#pragma unroll 1
+      for (int L = 0; L < S; ++L) {
+        float v[16];
+        tc::tmem_ld16(base + (uint32_t)(L * BN), v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) two_sum(hi[u], lo[u], v[u] * scale);
+        scale *= 0.00390625f;  // 2^-8
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&accempty[b]);
+    }
+    if (ok) {
+      const int64_t i = (int64_t)m0 + q * 32 + lane;
+      if (i < p.M) {
+        const int ei = p.ea[i];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int64_t jcol = (int64_t)n0 + h * 16 + u;
+          if (jcol < p.N) {
+            const double v = ldexp((double)hi[u] + (double)lo[u], ei + p.eb[jcol] - 16);
+            if (p.partial) p.C[((int64_t)split * p.N + jcol) * p.M + i] = v;
+            else p.C[jcol * p.ldc + i] = v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+__global__ void oz_sum_kernel(int64_t M, int64_t N, int nsplit, const double* __restrict__ part, double* C,
+                              int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / M, i = e - j * M;
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * total + e];
+    C[j * ldc + i] = acc;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    RC_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q));
+    RC_CHECK(q == cudaDriverEntryPointSuccess && ptr, RCHFSI_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+// All slices of an operand as one 2D BF16 tensor: S*R rows of Kp elements.
+CUtensorMap slice_map(const OzOperand& op, int box_rows) {
+  CUtensorMap m;
+  RC_CHECK(((uintptr_t)op.sl.p & 15) == 0 && (op.Kp * 2) % 16 == 0, RCHFSI_ERR_INVALID_ARG, "slice alignment");
+  cuuint64_t dims[2] = {(cuuint64_t)op.Kp, (cuuint64_t)(S * op.Rp)};
+  cuuint64_t strides[1] = {(cuuint64_t)(op.Kp * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)op.sl.p, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  RC_CHECK(r == CUDA_SUCCESS, RCHFSI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a slice tensor");
+  return m;
+}
+
+}  // namespace
+
+void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs, int64_t ks, OzOperand& op) {
+  RC_CHECK(R > 0 && K > 0, RCHFSI_ERR_INVALID_ARG, "oz_slice: empty operand");
+  RC_CHECK(ks == 1 || rs == 1, RCHFSI_ERR_INVALID_ARG, "oz_slice: one of the strides must be 1");
+  op.R = R;
+  op.Rp = std::max<int64_t>(R, 32);  // the 128-row TMA box must fit in the S * Rp rows of the tensor
+  op.K = K;
+  op.Kp = (K + KC - 1) / KC * KC;
+  op.sl.ensure((size_t)S * op.Rp * op.Kp);
+  op.ex.ensure((size_t)R);
+  if (op.Rp > R) RC_CUDA(cudaMemsetAsync(op.sl.p, 0, sizeof(__nv_bfloat16) * S * op.Rp * op.Kp, s));
+  if (ks == 1) {
+    rowexp_kcontig<<<cdiv(R, 8), 256, 0, s>>>(R, K, X, rs, op.ex.p);
+  } else {
+    rowexp_rcontig<<<cdiv(R, 256), 256, 0, s>>>(R, K, X, ks, op.ex.p);
+  }
+  RC_LAUNCH();
+  RC_CHECK(cdiv(R, 32) <= 65535u, RCHFSI_ERR_INVALID_ARG, "oz_slice: too many rows");
+  dim3 grid((unsigned)(op.Kp / KC), cdiv(R, 32));
+  slice_kernel<<<grid, dim3(32, 8), 0, s>>>(R, op.Rp, K, op.Kp, X, rs, ks, op.ex.p, op.sl.p);
+  RC_LAUNCH();
+}
+
+void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
+             DevBuf<double>& ws, int* err) {
+  RC_CHECK(A.K == B.K && A.Kp == B.Kp, RCHFSI_ERR_INVALID_ARG, "oz_gemm: K mismatch");
+  const int64_t M = A.R, N = B.R;
+  RC_CHECK(M < (1LL << 31) && N < (1LL << 31), RCHFSI_ERR_INVALID_ARG, "oz_gemm: too large");
+  const int m_tiles = (int)((M + BM - 1) / BM), n_tiles = (int)((N + BN - 1) / BN);
+  const int nchunks = (int)(A.Kp / KC);
+  const int tiles = m_tiles * n_tiles;
+  int nsplit = std::max(1, std::min(nchunks, num_sms / std::max(tiles, 1)));
+  const int per = (nchunks + nsplit - 1) / nsplit;
+  nsplit = (nchunks + per - 1) / per;
+  RC_CHECK(m_tiles <= 65535 && nsplit <= 65535, RCHFSI_ERR_INVALID_ARG, "oz_gemm: grid too large");
+  const CUtensorMap ma = slice_map(A, BM);
+  const CUtensorMap mb = slice_map(B, BN);
+  const size_t smem = (size_t)ASTAGES * kABytes + 2 * (size_t)kBBytes + 1024;
+  RC_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  OzArgs p;
+  p.M = (int)M;
+  p.N = (int)N;
+  p.MP = (int)A.Rp;
+  p.NP = (int)B.Rp;
+  p.chunks_per_split = per;
+  p.nchunks = nchunks;
+  p.ea = A.ex.p;
+  p.eb = B.ex.p;
+  p.err = err;
+  p.partial = nsplit > 1;
+  if (nsplit > 1) {
+    p.C = ws.ensure((size_t)nsplit * M * N);
+    p.ldc = M;
+  } else {
+    p.C = C;
+    p.ldc = ldc;
+  }
+  dim3 grid(n_tiles, m_tiles, nsplit);
+  {
+    // tensor-core flops of the 28 slice products; bytes: the slices once and the FP64 output
+    prof::Scope ps(s, RCHFSI_KERNEL_GEMM_F64_EMU, 2.0 * M * N * A.Kp * (S * (S + 1) / 2),
+                   2.0 * S * (double)(M + N) * A.Kp + 8.0 * M * N);
+    oz_gemm_kernel<<<grid, kThreads, smem, s>>>(ma, mb, p);
+    RC_LAUNCH();
+  }
+  if (nsplit > 1) {
+    const int64_t total = M * N;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+    oz_sum_kernel<<<blocks, 256, 0, s>>>(M, N, nsplit, p.C, C, ldc);
+    RC_LAUNCH();
+  }
+}
+
+}  // namespace rchfsi

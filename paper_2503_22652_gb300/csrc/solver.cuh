@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "fe.cuh"
+#include "oz_gemm.cuh"
 #include "prof.cuh"
 
 struct rchfsi_ctx;
@@ -26,6 +27,8 @@ struct Work {
   DevBuf<double> lz_v, lz_w, lz_vp, lz_t, lz_ab;  // Lanczos vectors and scalars
   DevBuf<double> syev_work;
   DevBuf<double> stage_in, stage_out;          // host <-> device staging (row-major)
+  OzOperand ozL, ozR, ozE;                     // FP64-emulation slices of the current operands
+  DevBuf<double> ozws;                         // split-K partials of the emulated FP64 GEMM
   void ensure(int64_t m_, int N_);
 };
 
@@ -34,10 +37,12 @@ struct DenseOp {
   DevBuf<double> AD64, DA64;              // filter operators A~ D^-1 and D^-1 A~, row-major
   DevBuf<float> AD32, DA32, ADtf, DAtf;   // FP32 copies (plain and TF32-rounded)
   DevBuf<__nv_bfloat16> AD16, DA16;       // BF16 copies
+  OzOperand ozA, ozB;                     // FP64-emulation slices of A and B (made on first use)
   bool has_B = false, has_dinv = false, has_dinv_dense = false;
   void reset() {
     A.release(); B.release(); Dinv.release(); Dinv_dense.release(); AD64.release(); DA64.release();
     AD32.release(); DA32.release(); ADtf.release(); DAtf.release(); AD16.release(); DA16.release();
+    ozA.sl.release(); ozA.ex.release(); ozB.sl.release(); ozB.ex.release(); ozA.R = ozB.R = 0;
     has_B = has_dinv = has_dinv_dense = false;
   }
 };
