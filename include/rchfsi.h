@@ -89,8 +89,14 @@ typedef struct rchfsi_params {
   int32_t rr_mode;       /* FP64 products of the residual / Rayleigh-Ritz steps: RCHFSI_RR_FP64 (FP64
                             arithmetic units) or RCHFSI_RR_FP64_EMULATED (FP64-accurate products from
                             exact BF16 slices on the tensor cores) */
-  int32_t reserved0;
+  int32_t eig_mode;      /* N x N projected eigenproblem: RCHFSI_EIG_SYEVD (cuSOLVER dsyevd, a library
+                            call) or RCHFSI_EIG_JACOBI (this library's parallel cyclic Jacobi kernel) */
 } rchfsi_params;
+
+typedef enum {
+  RCHFSI_EIG_SYEVD = 0,  /* divide and conquer (cuSOLVER) */
+  RCHFSI_EIG_JACOBI = 1  /* parallel cyclic Jacobi, one cooperative kernel, tolerance 1e-14 */
+} rchfsi_eig_mode;
 
 typedef enum {
   RCHFSI_RR_FP64 = 0,          /* FP64 FMA (DFMA) GEMMs */
@@ -145,7 +151,7 @@ typedef struct rchfsi_stats {
 
 /* Fill *p with defaults: nev = 1, block = 1, degree = 20, FP64, R-ChFSI, real, max_iter = 100,
  * min_iter = 0, lanczos_steps = 10, stall_iters = 0, fixed_bounds = 0, tol = 1e-8,
- * rr_mode = RCHFSI_RR_FP64. */
+ * rr_mode = RCHFSI_RR_FP64_EMULATED. */
 int rchfsi_params_default(rchfsi_params* p);
 
 /* Create a handle on the current CUDA device.  cuda_stream: a cudaStream_t to run on, or NULL

@@ -74,12 +74,14 @@ class Solver:
 
     def __init__(self, m, nev, block, degree=20, precision="fp64", method="rchfsi", max_iter=100,
                  min_iter=0, tol=1e-8, lanczos_steps=10, stall_iters=0, bounds=None,
-                 hbm_budget_bytes=0, stream=None, rr_mode=None):
+                 hbm_budget_bytes=0, stream=None, rr_mode=None, eig_mode=None):
         self.lib = _lib.load()
         p = rchfsi_params()
         self.lib.rchfsi_params_default(C.byref(p))
         if rr_mode is not None:
             p.rr_mode = _lib.RR_MODES[rr_mode] if isinstance(rr_mode, str) else int(rr_mode)
+        if eig_mode is not None:
+            p.eig_mode = _lib.EIG_MODES[eig_mode] if isinstance(eig_mode, str) else int(eig_mode)
         p.m, p.nev, p.block, p.degree = int(m), int(nev), int(block), int(degree)
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.method = METHOD_CHFSI if method == "chfsi" else METHOD_RCHFSI
@@ -123,6 +125,8 @@ class Solver:
                 v = METHOD_CHFSI if v == "chfsi" else METHOD_RCHFSI
             if k == "rr_mode" and isinstance(v, str):
                 v = _lib.RR_MODES[v]
+            if k == "eig_mode" and isinstance(v, str):
+                v = _lib.EIG_MODES[v]
             if k == "bounds":
                 p.fixed_bounds = 0 if v is None else 1
                 if v is not None:

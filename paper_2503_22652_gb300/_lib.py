@@ -31,6 +31,7 @@ OP_DENSE, OP_FE_CELL = 0, 1
 KERNEL_CLASSES = {"filter_tc": 0, "splitk_reduce": 1, "filter_simt": 2, "gemm_f64": 3, "fe_cell": 4,
                   "fe_cell_f64": 5, "gemm_f64_emu": 6}
 RR_MODES = {"fp64": 0, "emulated": 1}
+EIG_MODES = {"syevd": 0, "jacobi": 1}
 
 dptr = C.POINTER(C.c_double)
 
@@ -41,7 +42,7 @@ class rchfsi_params(C.Structure):
                 ("max_iter", C.c_int32), ("min_iter", C.c_int32), ("lanczos_steps", C.c_int32),
                 ("stall_iters", C.c_int32), ("fixed_bounds", C.c_int32), ("tol", C.c_double),
                 ("lmin", C.c_double), ("lT", C.c_double), ("lmax", C.c_double),
-                ("hbm_budget_bytes", C.c_uint64), ("rr_mode", C.c_int32), ("reserved0", C.c_int32)]
+                ("hbm_budget_bytes", C.c_uint64), ("rr_mode", C.c_int32), ("eig_mode", C.c_int32)]
 
 
 class rchfsi_operator(C.Structure):

@@ -84,6 +84,8 @@ void validate_params(const rchfsi_params* p) {
   RC_CHECK(p->block <= 6144, RCHFSI_ERR_UNSUPPORTED, "block larger than 6144");
   RC_CHECK(p->rr_mode == RCHFSI_RR_FP64 || p->rr_mode == RCHFSI_RR_FP64_EMULATED, RCHFSI_ERR_INVALID_ARG,
            "bad rr_mode");
+  RC_CHECK(p->eig_mode == RCHFSI_EIG_SYEVD || p->eig_mode == RCHFSI_EIG_JACOBI, RCHFSI_ERR_INVALID_ARG,
+           "bad eig_mode");
 }
 
 void need_op(rchfsi_ctx* h) {
@@ -262,6 +264,7 @@ int rchfsi_params_default(rchfsi_params* p) {
   p->lanczos_steps = 10;
   p->stall_iters = 0;
   p->fixed_bounds = 0;
+  p->rr_mode = RCHFSI_RR_FP64_EMULATED;
   p->tol = 1e-8;
   return RCHFSI_OK;
 }

@@ -438,7 +438,7 @@ void filter_internal(rchfsi_ctx& c, const double* X, const double* lam_host, con
 }
 
 // ------------------------------------------------------------------ Rayleigh-Ritz (FP64)
-static void syevd(rchfsi_ctx& c, int n, double* A, double* w) {
+[[maybe_unused]] static void syevd(rchfsi_ctx& c, int n, double* A, double* w) {
   if (!c.solver) {
     RC_CHECK(cusolverDnCreate(&c.solver) == CUSOLVER_STATUS_SUCCESS, RCHFSI_ERR_CUDA, "cusolverDnCreate failed");
   }
@@ -518,7 +518,13 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   transpose_f64(c.s, N, N, w.GA.p, N, w.Z.p, N);
   trsm_lower_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
   symmetrize_f64(c.s, N, w.Z.p, N);
-  syevd(c, N, w.Z.p, evals);
+  // eigenpairs of the projected matrix (eigenvectors overwrite Z)
+  if (c.p.eig_mode == RCHFSI_EIG_JACOBI) {
+    jacobi_eig_f64(c.s, N, w.Z.p, w.Zt.p, evals, w.syev_work, 1e-14, 60);
+    RC_CUDA(cudaMemcpyAsync(w.Z.p, w.Zt.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));
+  } else {
+    syevd(c, N, w.Z.p, evals);
+  }
   // E = L^-T V
   trsm_lower_trans_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
   // X = Y E, AX = AY E, BX = BY E

@@ -153,6 +153,9 @@ int cholesky_f64(cudaStream_t s, int n, double* A, int lda, int* d_info);  // lo
 void trsm_lower_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
 void trsm_lower_trans_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
 void symmetrize_f64(cudaStream_t s, int n, double* A, int lda);
+// Symmetric eigensolver (parallel cyclic Jacobi, jacobi.cu): M destroyed; V, evals ascending.
+int jacobi_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, double tol,
+                   int max_sweeps);
 
 // Lanczos vector helpers
 void dot_f64(cudaStream_t s, int64_t n, const double* x, const double* y, double* out);

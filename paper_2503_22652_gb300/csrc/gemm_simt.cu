@@ -133,6 +133,34 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(int64_t M, int64_t N, int
   }
 }
 
+// Matrix-vector shapes (N <= 4, A K-contiguous): one warp per output row, lanes over K.  The tiled
+// kernel would compute a 64-wide tile for each of these columns.
+template <typename T, bool BKC>
+__global__ void __launch_bounds__(256) gemv_kernel(int64_t M, int N, int64_t K, const T* __restrict__ A, int64_t lda,
+                                                   const T* __restrict__ B, int64_t ldb, EpiDev<T> epi) {
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= M) return;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  const T* arow = A + i * lda;
+  for (int64_t k = lane; k < K; k += 32) {
+    const T a = arow[k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < N) acc[j] = fma(a, BKC ? B[(int64_t)j * ldb + k] : B[k * ldb + j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+  if (lane < N) {
+    T v = acc[0];
+#pragma unroll
+    for (int j = 1; j < 4; ++j)
+      if (lane == j) v = acc[j];
+    epi(i, lane, v);
+  }
+}
+
 template <typename T>
 __global__ void splitk_sum_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ partial, EpiDev<T> epi) {
   const int64_t total = M * N;
@@ -175,6 +203,14 @@ template <typename T>
 void gemm_dispatch(cudaStream_t s, int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, bool ak, const T* B,
                    int64_t ldb, bool bk, const EpiArgs& epi) {
   if (M <= 0 || N <= 0) return;
+  if (N <= 4 && ak) {
+    EpiDev<T> d = to_dev<T>(epi);
+    prof::Scope ps(s, epi.prof_cls, 2.0 * M * N * K, (double)sizeof(T) * ((double)M * K + (double)K * N + M * N));
+    if (bk) gemv_kernel<T, true><<<cdiv(M, 8), 256, 0, s>>>(M, (int)N, K, A, lda, B, ldb, d);
+    else gemv_kernel<T, false><<<cdiv(M, 8), 256, 0, s>>>(M, (int)N, K, A, lda, B, ldb, d);
+    RC_LAUNCH();
+    return;
+  }
   RC_CHECK(cdiv(M, BM) <= 65535u, RCHFSI_ERR_INVALID_ARG, "gemm: M too large for the grid");
   const int64_t tiles = (int64_t)cdiv(N, BN) * cdiv(M, BM);
   // split K when the output alone cannot fill the GPU (target ~4 CTAs per SM, slices >= 256)

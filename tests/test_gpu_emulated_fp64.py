@@ -71,3 +71,29 @@ def test_solve_emulated_rr_fe():
     X, ev, res, st = s.solve(wl.gaussian_block(p["m"], 12, seed=2))
     assert st["max_rel_residual"] <= 1e-8
     np.testing.assert_allclose(ev[:7], ref, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("m,N,gen", [(280, 36, True), (333, 9, False), (120, 1, False), (64, 17, False)])
+def test_rayleigh_ritz_jacobi_eigensolver(m, N, gen):
+    """This library's Jacobi eigensolver for the projected matrix gives the oracle's Ritz pairs."""
+    case = dense_case(m=m, N=N, generalized=gen)
+    Bm = case["B"] if gen else np.eye(m)
+    s = make_solver(case, N, eig_mode="jacobi")
+    X, ev = s.rayleigh_ritz(case["X"])
+    Xr, evr, _, _ = rr.rayleigh_ritz(case["X"], lambda v: case["A"] @ v, lambda v: Bm @ v)
+    np.testing.assert_allclose(ev, evr, rtol=1e-11, atol=1e-11 * np.abs(evr).max())
+    assert np.all(np.diff(ev) >= 0)
+    np.testing.assert_allclose(X.T @ Bm @ X, np.eye(N), atol=1e-11)
+    sg = np.sign(np.sum(X * (Bm @ Xr), axis=0))
+    assert relfro(X * sg[None, :], Xr) <= 1e-9
+
+
+def test_solve_jacobi_eigensolver():
+    m = 600
+    c = wl.dense_config2(m=m)
+    ref = sla.eigh(c["A"], c["B"], eigvals_only=True)[:30]
+    s = Solver(m, nev=30, block=40, degree=30, precision="tf32", max_iter=200, eig_mode="jacobi")
+    s.set_dense(c["A"], B=c["B"], Dinv=c["Dinv"])
+    X, ev, res, st = s.solve(wl.gaussian_block(m, 40, seed=2))
+    assert st["max_rel_residual"] <= 1e-8
+    np.testing.assert_allclose(ev[:30], ref, atol=1e-9 * np.abs(ref).max())
