@@ -21,8 +21,15 @@
  *   - Calls on one handle are serialised on the handle's CUDA stream and return after the result
  *     is complete (the stream is synchronised before returning).  A handle must not be used by
  *     two host threads at once.  Different handles are independent.
- *   - Only real symmetric problems are implemented (field = RCHFSI_REAL); RCHFSI_COMPLEX returns
- *     RCHFSI_ERR_UNSUPPORTED.
+ *   - Complex Hermitian problems (field = RCHFSI_COMPLEX, e.g. the Bloch k-point operators of
+ *     Section 4.2) take complex blocks X, W, Y_p, the dense A and the cell matrices A_cells as
+ *     interleaved (re, im) pairs of doubles, i.e. C99 `double complex` / NumPy complex128 arrays of
+ *     the same shape, row-major.  B, B_cells, Dinv and every eigenvalue / residual array stay
+ *     real.  Internally the library solves the real symmetric embedding
+ *     [[Ar, -Ai], [Ai, Ar]] of order 2m with the block [[Xr, -Xi], [Xi, Xr]] of 2N columns; each
+ *     complex eigenpair appears twice there, and one representative per pair is returned.  The
+ *     filter runs on N embedded columns only (the other N are their products with i).  block is
+ *     limited to 3072 for complex problems.  A_filter and Dinv_dense are real-only.
  */
 #ifndef RCHFSI_H
 #define RCHFSI_H
@@ -167,7 +174,8 @@ int rchfsi_set_params(struct rchfsi_ctx* h, const rchfsi_params* p);
 
 /* Upload the operator (copied to device memory) and precompute what the filter needs:
  * A D^-1 for Algorithm 3 and D^-1 A for Algorithm 2 (dense), and the reduced-precision copies.
- * Errors: INVALID_ARG (sizes/pointers), UNSUPPORTED (complex), OOM. */
+ * Errors: INVALID_ARG (sizes/pointers, field differing from the handle's), UNSUPPORTED
+ * (A_filter or Dinv_dense with a complex operator), OOM. */
 int rchfsi_set_operator(struct rchfsi_ctx* h, const rchfsi_operator* op);
 
 /* ---------------------------------------------------------------- the filter (Algorithm 3) */

@@ -2,7 +2,9 @@
 
 The binding only marshals arguments: NumPy arrays (host memory) and torch tensors (host or CUDA
 memory) are passed to the library as raw pointers; every step of the method runs in
-librchfsi.so.  Blocks are (m, N) float64 arrays in row-major (C) order.
+librchfsi.so.  Blocks are (m, N) float64 arrays in row-major (C) order; for complex Hermitian
+problems (field="complex") blocks, A and the FE cell matrices A_c are complex128 (interleaved
+real/imaginary parts) while B, B_c and D^-1 stay real.
 
     from paper_2503_22652_gb300 import Solver
     s = Solver(m, nev=50, block=60, degree=20, precision="tf32")
@@ -53,6 +55,8 @@ def _check_arr(a, shape, name, dtype=np.float64):
     # torch tensor
     if not a.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
+    if a.is_complex() != (dtype == np.complex128) or a.element_size() != np.dtype(dtype).itemsize:
+        raise ValueError("%s: expected a %s tensor" % (name, np.dtype(dtype).name))
     if a.numel() != int(np.prod(shape)):
         raise ValueError("%s: expected %s elements" % (name, int(np.prod(shape))))
     return a
@@ -62,11 +66,12 @@ def _is_cuda(a):
     return hasattr(a, "is_cuda") and a.is_cuda
 
 
-def _empty_like_kind(ref, shape):
+def _empty_like_kind(ref, shape, dtype=np.float64):
     if _is_cuda(ref):
         import torch
-        return torch.empty(shape, dtype=torch.float64, device=ref.device)
-    return np.empty(shape, dtype=np.float64)
+        tdt = torch.complex128 if dtype == np.complex128 else torch.float64
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype)
 
 
 class Solver:
@@ -74,7 +79,7 @@ class Solver:
 
     def __init__(self, m, nev, block, degree=20, precision="fp64", method="rchfsi", max_iter=100,
                  min_iter=0, tol=1e-8, lanczos_steps=10, stall_iters=0, bounds=None,
-                 hbm_budget_bytes=0, stream=None, rr_mode=None, eig_mode=None):
+                 hbm_budget_bytes=0, stream=None, rr_mode=None, eig_mode=None, field="real"):
         self.lib = _lib.load()
         p = rchfsi_params()
         self.lib.rchfsi_params_default(C.byref(p))
@@ -91,6 +96,9 @@ class Solver:
             p.fixed_bounds = 1
             p.lmin, p.lT, p.lmax = (float(b) for b in bounds)
         p.hbm_budget_bytes = int(hbm_budget_bytes)
+        self.complex = field == "complex"
+        p.field = _lib.COMPLEX if self.complex else _lib.REAL
+        self.dt = np.complex128 if self.complex else np.float64  # dtype of blocks and of A / A_c
         self.params = p
         self.m, self.N = int(m), int(block)
         h = C.c_void_p()
@@ -138,13 +146,13 @@ class Solver:
     # ------------------------------------------------------------ operators
     def set_dense(self, A, B=None, Dinv=None, Dinv_dense=None, A_filter=None):
         m = self.m
-        A = _check_arr(A, (m, m), "A")
+        A = _check_arr(A, (m, m), "A", self.dt)
         B = _check_arr(B, (m, m), "B")
         Dinv = _check_arr(Dinv, (m,), "Dinv")
         Dinv_dense = _check_arr(Dinv_dense, (m, m), "Dinv_dense")
         A_filter = _check_arr(A_filter, (m, m), "A_filter")
         op = rchfsi_operator()
-        op.kind, op.field, op.m = _lib.OP_DENSE, _lib.REAL, m
+        op.kind, op.field, op.m = _lib.OP_DENSE, self.params.field, m
         op.A, op.B, op.Dinv, op.Dinv_dense, op.A_filter = (ptr(A), ptr(B), ptr(Dinv), ptr(Dinv_dense),
                                                            ptr(A_filter))
         self._check(self.lib.rchfsi_set_operator(self.h, C.byref(op)), self.h)
@@ -154,11 +162,11 @@ class Solver:
             else cell_dofs
         nC, nc = cell_dofs.shape
         shared = tuple(B_cells.shape) == (nc, nc)
-        A_cells = _check_arr(A_cells, (nC, nc, nc), "A_cells")
+        A_cells = _check_arr(A_cells, (nC, nc, nc), "A_cells", self.dt)
         B_cells = _check_arr(B_cells, (nc, nc) if shared else (nC, nc, nc), "B_cells")
         Dinv = _check_arr(Dinv, (self.m,), "Dinv")
         op = rchfsi_operator()
-        op.kind, op.field, op.m = _lib.OP_FE_CELL, _lib.REAL, self.m
+        op.kind, op.field, op.m = _lib.OP_FE_CELL, self.params.field, self.m
         op.n_cells, op.n_c, op.B_cells_shared = nC, nc, 1 if shared else 0
         op.cell_dofs, op.A_cells, op.B_cells, op.Dinv = ptr(cell_dofs), ptr(A_cells), ptr(B_cells), ptr(Dinv)
         self._check(self.lib.rchfsi_set_operator(self.h, C.byref(op)), self.h)
@@ -166,41 +174,41 @@ class Solver:
     # ------------------------------------------------------------ the method
     def filter(self, X, lam, W, lmin, lT, lmax, degree, out=None):
         """Algorithm 3 (rchfsi_filter)."""
-        X = _check_arr(X, (self.m, self.N), "X")
-        W = _check_arr(W, (self.m, self.N), "W")
+        X = _check_arr(X, (self.m, self.N), "X", self.dt)
+        W = _check_arr(W, (self.m, self.N), "W", self.dt)
         lam = _check_arr(lam, (self.N,), "Lambda")
         if out is None:
-            out = _empty_like_kind(X, (self.m, self.N))
+            out = _empty_like_kind(X, (self.m, self.N), self.dt)
         self._check(self.lib.rchfsi_filter(self.h, ptr(X), ptr(lam), ptr(W), lmin, lT, lmax, int(degree),
                                            ptr(out)), self.h)
         return out
 
     def chfsi_filter(self, X, lmin, lT, lmax, degree, out=None):
         """Algorithm 2 (rchfsi_chfsi_filter)."""
-        X = _check_arr(X, (self.m, self.N), "X")
+        X = _check_arr(X, (self.m, self.N), "X", self.dt)
         if out is None:
-            out = _empty_like_kind(X, (self.m, self.N))
+            out = _empty_like_kind(X, (self.m, self.N), self.dt)
         self._check(self.lib.rchfsi_chfsi_filter(self.h, ptr(X), lmin, lT, lmax, int(degree), ptr(out)),
                     self.h)
         return out
 
     def residual(self, X, lam):
-        X = _check_arr(X, (self.m, self.N), "X")
+        X = _check_arr(X, (self.m, self.N), "X", self.dt)
         lam = _check_arr(lam, (self.N,), "Lambda")
-        W = _empty_like_kind(X, (self.m, self.N))
+        W = _empty_like_kind(X, (self.m, self.N), self.dt)
         r = np.empty(self.N)
         self._check(self.lib.rchfsi_residual(self.h, ptr(X), ptr(lam), ptr(W), ptr(r)), self.h)
         return W, r
 
     def rayleigh_ritz(self, Y):
-        Y = _check_arr(Y, (self.m, self.N), "Y")
-        X = _empty_like_kind(Y, (self.m, self.N))
+        Y = _check_arr(Y, (self.m, self.N), "Y", self.dt)
+        X = _empty_like_kind(Y, (self.m, self.N), self.dt)
         ev = np.empty(self.N)
         self._check(self.lib.rchfsi_rayleigh_ritz(self.h, ptr(Y), ptr(X), ptr(ev)), self.h)
         return X, ev
 
     def lanczos_bounds(self, v0, steps=10):
-        v0 = _check_arr(v0, (self.m,), "v0")
+        v0 = _check_arr(v0, (self.m,), "v0", self.dt)
         lmax, nA = C.c_double(), C.c_double()
         self._check(self.lib.rchfsi_lanczos_bounds(self.h, ptr(v0), int(steps), C.byref(lmax), C.byref(nA)),
                     self.h)
@@ -209,7 +217,7 @@ class Solver:
     def solve(self, X0, allow_not_converged=False):
         """Algorithm 1 (rchfsi_solve).  Returns (X, evals, rel_resid, stats_dict)."""
         X = X0.copy() if isinstance(X0, np.ndarray) else X0.clone()
-        X = _check_arr(X, (self.m, self.N), "X0")
+        X = _check_arr(X, (self.m, self.N), "X0", self.dt)
         ev = np.empty(self.N)
         res = np.empty(self.N)
         hist = np.full(self.params.max_iter + 1, np.nan)
@@ -254,25 +262,28 @@ class Server:
         p = rq.params
         lib.rchfsi_params_default(C.byref(p))
         p.m, p.nev, p.block = int(m), int(nev), int(block)
+        cplx = params.pop("field", "real") == "complex"
+        dt = np.complex128 if cplx else np.float64
+        p.field = _lib.COMPLEX if cplx else _lib.REAL
         for k, v in params.items():
             if k == "precision" and isinstance(v, str):
                 v = PRECISIONS[v]
             setattr(p, k, v)
         keep = []
         op = rq.op
-        op.m, op.field = int(m), _lib.REAL
+        op.m, op.field = int(m), p.field
         if dense is not None:
             op.kind = _lib.OP_DENSE
             for k in ("A", "B", "Dinv"):
                 a = dense.get(k)
                 if a is not None:
-                    a = np.ascontiguousarray(a, dtype=np.float64)
+                    a = np.ascontiguousarray(a, dtype=dt if k == "A" else np.float64)
                     keep.append(a)
                     setattr(op, k, a.ctypes.data)
         else:
             op.kind = _lib.OP_FE_CELL
             dofs = np.ascontiguousarray(fe["cell_dofs"], dtype=np.int32)
-            Ac = np.ascontiguousarray(fe["A_cells"], dtype=np.float64)
+            Ac = np.ascontiguousarray(fe["A_cells"], dtype=dt)
             Bc = np.ascontiguousarray(fe["B_cells"], dtype=np.float64)
             Dv = np.ascontiguousarray(fe["Dinv"], dtype=np.float64)
             keep += [dofs, Ac, Bc, Dv]
@@ -281,7 +292,7 @@ class Server:
             op.cell_dofs, op.A_cells, op.B_cells, op.Dinv = (dofs.ctypes.data, Ac.ctypes.data, Bc.ctypes.data,
                                                              Dv.ctypes.data)
         if X0 is not None:
-            X0 = np.ascontiguousarray(X0, dtype=np.float64)
+            X0 = np.ascontiguousarray(X0, dtype=dt)
             keep.append(X0)
             rq.X0 = X0.ctypes.data
         rq.warm_key = int(warm_key)
@@ -289,17 +300,17 @@ class Server:
         rc = lib.rchfsi_submit(self.h, C.byref(rq), C.byref(t))
         if rc != OK:
             raise RChFSIError(rc, "submit")
-        self._pending[t.value] = (int(m), int(block))
+        self._pending[t.value] = (int(m), int(block), dt)
         return t.value
 
     def poll(self, ticket, want_vectors=False):
         """None while pending, else dict(status, iterations, max_rel_residual, latency_ms,
         queue_ms, evals[, X])."""
-        m, N = self._pending[ticket]
+        m, N, dt = self._pending[ticket]
         res = rchfsi_result()
         ev = np.empty(N)
         res.evals = ev.ctypes.data
-        X = np.empty((m, N)) if want_vectors else None
+        X = np.empty((m, N), dtype=dt) if want_vectors else None
         if X is not None:
             res.X = X.ctypes.data
         rc = self.lib.rchfsi_poll(self.h, int(ticket), C.byref(res))

@@ -76,12 +76,12 @@ void validate_params(const rchfsi_params* p) {
   RC_CHECK(p->method == RCHFSI_METHOD_RCHFSI || p->method == RCHFSI_METHOD_CHFSI, RCHFSI_ERR_INVALID_ARG,
            "bad method");
   RC_CHECK(p->field == RCHFSI_REAL || p->field == RCHFSI_COMPLEX, RCHFSI_ERR_INVALID_ARG, "bad field");
-  RC_CHECK(p->field == RCHFSI_REAL, RCHFSI_ERR_UNSUPPORTED, "complex Hermitian problems are not implemented");
   RC_CHECK(p->max_iter >= 0 && p->min_iter >= 0, RCHFSI_ERR_INVALID_ARG, "iteration counts must be >= 0");
   RC_CHECK(p->lanczos_steps >= 2 && p->lanczos_steps <= p->m, RCHFSI_ERR_INVALID_ARG,
            "lanczos_steps must be in [2, m]");
   RC_CHECK(p->tol >= 0.0, RCHFSI_ERR_INVALID_ARG, "tol must be >= 0");
-  RC_CHECK(p->block <= 6144, RCHFSI_ERR_UNSUPPORTED, "block larger than 6144");
+  RC_CHECK(p->block * (p->field == RCHFSI_COMPLEX ? 2 : 1) <= 6144, RCHFSI_ERR_UNSUPPORTED,
+           "block larger than 6144 (3072 for complex problems)");
   RC_CHECK(p->rr_mode == RCHFSI_RR_FP64 || p->rr_mode == RCHFSI_RR_FP64_EMULATED, RCHFSI_ERR_INVALID_ARG,
            "bad rr_mode");
   RC_CHECK(p->eig_mode == RCHFSI_EIG_SYEVD || p->eig_mode == RCHFSI_EIG_JACOBI, RCHFSI_ERR_INVALID_ARG,
@@ -143,6 +143,143 @@ std::vector<double> host_vec(rchfsi_ctx& c, const double* src, size_t n) {
   return v;
 }
 
+// ------------------------------------------------------------------ complex problems (real embedding)
+// Caller block (real m x N row-major, or complex m x N interleaved) -> internal column-major block.
+void load_any(rchfsi_ctx& c, const double* src, double* dst_col) {
+  if (!c.cplx) {
+    load_block(c, src, dst_col);
+    return;
+  }
+  RC_CHECK(src, RCHFSI_ERR_INVALID_ARG, "NULL block argument");
+  const size_t n = 2 * (size_t)c.mc * c.Nc;
+  double* st = c.cstage.ensure(n);
+  const auto kind = is_device_pointer(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  RC_CUDA(cudaMemcpyAsync(st, src, n * sizeof(double), kind, c.s));
+  cplx_embed_block(c.s, c.mc, c.Nc, st, dst_col);
+}
+
+// Eigenvalue-like vectors: N caller values -> the internal block's (duplicated for complex).
+std::vector<double> lam_any(rchfsi_ctx& c, const double* Lambda) {
+  if (!c.cplx) return host_vec(c, Lambda, c.p.block);
+  std::vector<double> v = host_vec(c, Lambda, c.Nc);
+  v.insert(v.end(), v.begin(), v.end());
+  return v;
+}
+
+// Internal column-major block -> caller block; for complex problems the embedded columns `cols`
+// become the caller's complex columns (default: the first Nc, the embedding of the input block).
+void store_any(rchfsi_ctx& c, const double* src_col, double* dst, const std::vector<int>* cols = nullptr) {
+  if (!dst) return;
+  if (!c.cplx) {
+    store_block(c, src_col, dst);
+    return;
+  }
+  std::vector<int> idx(c.Nc);
+  for (int j = 0; j < c.Nc; ++j) idx[j] = cols ? (*cols)[j] : j;
+  int* dcols = c.ccols.ensure(c.Nc);
+  RC_CUDA(cudaMemcpyAsync(dcols, idx.data(), sizeof(int) * c.Nc, cudaMemcpyHostToDevice, c.s));
+  const size_t n = 2 * (size_t)c.mc * c.Nc;
+  if (is_device_pointer(dst)) {
+    cplx_extract_cols(c.s, c.mc, c.Nc, src_col, dcols, dst);
+  } else {
+    double* st = c.cstage.ensure(n);
+    cplx_extract_cols(c.s, c.mc, c.Nc, src_col, dcols, st);
+    RC_CUDA(cudaMemcpyAsync(dst, st, n * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  }
+  RC_CUDA(cudaStreamSynchronize(c.s));  // idx must outlive the copy
+}
+
+// Choose, among the 2N embedded Ritz vectors (ascending eigenvalues ev), N that represent distinct
+// complex eigenvectors.  Each complex eigenpair appears as two real ones with equal eigenvalues,
+// spanning {x, i x}; for an isolated pair the first member is taken.  A cluster of more than two
+// equal eigenvalues (a complex eigenvalue of multiplicity > 1) is orthonormalised in the complex
+// B inner product (Gram-Schmidt on the device, using B X), dropping members that depend on the ones
+// already kept.  X, AX and BX (column-major, 2m rows; AX may be null) receive the same column
+// operations, so they stay consistent.
+std::vector<int> select_complex(rchfsi_ctx& c, const std::vector<double>& ev, double* X, double* AX, double* BX) {
+  const int n2 = (int)ev.size();
+  double scale = 1e-300;
+  for (double v : ev) scale = std::max(scale, std::fabs(v));
+  const double thr = 1e-9 * scale;
+  std::vector<int> out;
+  double* d = c.cdot.ensure(2);
+  int k = 0;
+  while (k < n2 && (int)out.size() < c.Nc) {
+    int e = k + 1;
+    while (e < n2 && std::fabs(ev[e] - ev[k]) <= thr) ++e;
+    const int size = e - k;
+    if (size <= 2) {
+      out.push_back(k);
+    } else {
+      std::vector<int> kept;
+      for (int j = k; j < e && (int)kept.size() < size / 2; ++j) {
+        for (int l : kept) {
+          double h[2];
+          cplx_dot(c.s, c.mc, X, BX, l, j, d);
+          RC_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+          RC_CUDA(cudaStreamSynchronize(c.s));
+          cplx_axpy(c.s, c.mc, X, AX, BX, l, j, h[0], h[1], 1.0);
+        }
+        double h[2];
+        cplx_dot(c.s, c.mc, X, BX, j, j, d);
+        RC_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+        RC_CUDA(cudaStreamSynchronize(c.s));
+        if (h[0] > 0.25) {
+          cplx_axpy(c.s, c.mc, X, AX, BX, j, j, 0.0, 0.0, 1.0 / std::sqrt(h[0]));
+          kept.push_back(j);
+        }
+      }
+      for (int j : kept)
+        if ((int)out.size() < c.Nc) out.push_back(j);
+    }
+    k = e;
+  }
+  RC_CHECK((int)out.size() == c.Nc, RCHFSI_ERR_NUMERIC, "complex eigenpairs could not be paired");
+  return out;
+}
+
+// After a Rayleigh-Ritz step of a complex problem: keep one real representative of each complex
+// Ritz pair and rebuild X, AX, BX as [X_s, J X_s] (J = multiplication by i), so that the first N
+// columns carry the complex block and the filter needs to run on them only.  ev (2N ascending
+// values) becomes [ev_s, ev_s], also on the device.
+void pair_complex(rchfsi_ctx& c, std::vector<double>& ev) {
+  Work& w = c.w;
+  const std::vector<int> sel = select_complex(c, ev, w.X.p, w.AX.p, w.BX.p);
+  int* dcols = c.ccols.ensure(c.Nc);
+  RC_CUDA(cudaMemcpyAsync(dcols, sel.data(), sizeof(int) * c.Nc, cudaMemcpyHostToDevice, c.s));
+  const size_t blk = (size_t)c.p.m * c.p.block;
+  for (double* b : {w.X.p, w.AX.p, w.BX.p}) {
+    cplx_rebuild(c.s, c.mc, c.Nc, b, dcols, w.T1.p);
+    RC_CUDA(cudaMemcpyAsync(b, w.T1.p, blk * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+  }
+  std::vector<double> e2(2 * c.Nc);
+  for (int j = 0; j < c.Nc; ++j) e2[j] = e2[c.Nc + j] = ev[sel[j]];
+  ev = e2;
+  RC_CUDA(cudaMemcpyAsync(w.evals.p, ev.data(), ev.size() * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));  // sel and ev must outlive the copies
+}
+
+// Filter of the caller-facing block.  A complex block's embedding [[Xr, -Xi], [Xi, Xr]] is closed
+// under J, and the embedded A, B, D^-1 commute with J, so only its first N columns are filtered;
+// `complete` fills the other N with J times them.
+void filter_any(rchfsi_ctx& c, const double* X, const double* lam, const double* W, double lmin, double lT,
+                double lmax, int p, double* Y, bool chfsi, bool complete) {
+  if (!c.cplx) {
+    filter_internal(c, X, lam, W, lmin, lT, lmax, p, Y, chfsi);
+    return;
+  }
+  const int saved = c.p.block;
+  c.p.block = c.Nc;
+  try {
+    filter_internal(c, X, lam, W, lmin, lT, lmax, p, Y, chfsi);
+  } catch (...) {
+    c.p.block = saved;
+    throw;
+  }
+  c.p.block = saved;
+  if (complete) cplx_rebuild(c.s, c.mc, c.Nc, Y, nullptr, Y);
+}
+
 void set_dense(rchfsi_ctx& c, const rchfsi_operator* op) {
   const int64_t m = c.p.m;
   const size_t mm = (size_t)m * m;
@@ -202,6 +339,7 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
            "A_filter / Dinv_dense are for dense operators");
   c.fe.reset(new FeOp());
   FeOp& f = *c.fe;
+  const int64_t mc = c.cplx ? c.mc : c.p.m;  // dofs of the (complex) problem
   f.m = c.p.m;
   f.n_cells = op->n_cells;
   f.nc = op->n_c;
@@ -216,13 +354,66 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
   RC_CUDA(cudaMemcpyAsync(hd.data(), dofs, nd * sizeof(int), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaStreamSynchronize(c.s));
   for (size_t i = 0; i < nd; ++i)
-    RC_CHECK(hd[i] >= 0 && hd[i] < c.p.m, RCHFSI_ERR_INVALID_ARG, "cell_dofs entry out of [0, m)");
-  to_device(c, op->A_cells, f.A64.ensure(na), na);
+    RC_CHECK(hd[i] >= 0 && hd[i] < mc, RCHFSI_ERR_INVALID_ARG, "cell_dofs entry out of [0, m)");
   const size_t nb = f.B_shared ? (size_t)f.nc * f.nc : na;
   to_device(c, op->B_cells, f.B64.ensure(nb), nb);
-  to_device(c, op->Dinv, f.Dinv.ensure(c.p.m), c.p.m);
   f.err = c.w.info.p + 2;
+  if (!c.cplx) {
+    to_device(c, op->A_cells, f.A64.ensure(na), na);
+    to_device(c, op->Dinv, f.Dinv.ensure(c.p.m), c.p.m);
+  } else {
+    // complex cell matrices: real parts in this operator, imaginary parts in f.imag
+    f.cplx = true;
+    f.mc = mc;
+    f.imag.reset(new FeOp());
+    FeOp& g = *f.imag;
+    g.m = c.p.m;
+    g.mc = mc;
+    g.n_cells = f.n_cells;
+    g.nc = f.nc;
+    g.err = f.err;
+    DevBuf<double> tmp;
+    to_device(c, op->A_cells, tmp.ensure(2 * na), 2 * na);
+    cplx_deinterleave(c.s, na, tmp.p, f.A64.ensure(na), g.A64.ensure(na));
+    RC_CUDA(cudaMemcpyAsync(g.dofs.ensure(nd), dofs, nd * sizeof(int), cudaMemcpyDeviceToDevice, c.s));
+    // D^-1 of the embedding: [D^-1; D^-1]
+    double* dv = f.Dinv.ensure(2 * mc);
+    to_device(c, op->Dinv, dv, mc);
+    RC_CUDA(cudaMemcpyAsync(dv + mc, dv, mc * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(g.Dinv.ensure(2 * mc), dv, 2 * mc * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+  }
   RC_CUDA(cudaStreamSynchronize(c.s));
+}
+
+// Complex Hermitian dense operator: build the real embedding on the device and set it.
+void set_dense_complex(rchfsi_ctx& c, const rchfsi_operator* op) {
+  const int64_t mc = c.mc, m2 = 2 * mc;
+  RC_CHECK(op->A, RCHFSI_ERR_INVALID_ARG, "dense operator needs A");
+  RC_CHECK(!op->A_filter && !op->Dinv_dense, RCHFSI_ERR_UNSUPPORTED,
+           "A_filter / Dinv_dense are not available for complex operators");
+  DevBuf<double> ac, ae, bc, be, de;
+  to_device(c, op->A, ac.ensure(2 * (size_t)mc * mc), 2 * (size_t)mc * mc);
+  cplx_embed_dense(c.s, mc, ac.p, ae.ensure((size_t)m2 * m2));
+  ac.release();
+  rchfsi_operator e{};
+  e.kind = RCHFSI_OP_DENSE;
+  e.field = RCHFSI_REAL;
+  e.m = m2;
+  e.A = ae.p;
+  if (op->B) {
+    to_device(c, op->B, bc.ensure((size_t)mc * mc), (size_t)mc * mc);
+    cplx_embed_blockdiag(c.s, mc, bc.p, be.ensure((size_t)m2 * m2));
+    e.B = be.p;
+  }
+  if (op->Dinv) {
+    double* dv = de.ensure(m2);
+    to_device(c, op->Dinv, dv, mc);
+    RC_CUDA(cudaMemcpyAsync(dv + mc, dv, mc * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    e.Dinv = dv;
+  }
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  set_dense(c, &e);
 }
 
 }  // namespace
@@ -276,6 +467,17 @@ int rchfsi_create(rchfsi_ctx** out, const rchfsi_params* p, void* cuda_stream) {
   const int rc = guarded(h, [&] {
     validate_params(p);
     h->p = *p;
+    if (p->field == RCHFSI_COMPLEX) {
+      // the real embedding: twice the rows, twice the block, twice the wanted pairs
+      h->cplx = true;
+      h->mc = p->m;
+      h->Nc = p->block;
+      h->nevc = p->nev;
+      h->p.m = 2 * p->m;
+      h->p.block = 2 * p->block;
+      h->p.nev = 2 * p->nev;
+      h->p.field = RCHFSI_REAL;
+    }
     RC_CUDA(cudaGetDevice(&h->device));
     RC_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     if (cuda_stream) {
@@ -285,7 +487,7 @@ int rchfsi_create(rchfsi_ctx** out, const rchfsi_params* p, void* cuda_stream) {
       h->own_stream = true;
     }
     for (auto& e : h->ev) RC_CUDA(cudaEventCreate(&e));
-    h->w.ensure(p->m, p->block);
+    h->w.ensure(h->p.m, h->p.block);
     return RCHFSI_OK;
   });
   if (rc != RCHFSI_OK) {
@@ -313,9 +515,19 @@ int rchfsi_set_params(rchfsi_ctx* h, const rchfsi_params* p) {
   if (!h) return RCHFSI_ERR_INVALID_ARG;
   return guarded(h, [&] {
     validate_params(p);
-    RC_CHECK(p->m == h->p.m && p->block == h->p.block && p->field == h->p.field, RCHFSI_ERR_INVALID_ARG,
+    const bool cp = p->field == RCHFSI_COMPLEX;
+    const int64_t m0 = h->cplx ? h->mc : h->p.m;
+    const int n0 = h->cplx ? h->Nc : h->p.block;
+    RC_CHECK(p->m == m0 && p->block == n0 && cp == h->cplx, RCHFSI_ERR_INVALID_ARG,
              "m, block and field cannot change on an existing handle");
     h->p = *p;
+    if (cp) {
+      h->nevc = p->nev;
+      h->p.m = 2 * p->m;
+      h->p.block = 2 * p->block;
+      h->p.nev = 2 * p->nev;
+      h->p.field = RCHFSI_REAL;
+    }
     return RCHFSI_OK;
   });
 }
@@ -324,10 +536,14 @@ int rchfsi_set_operator(rchfsi_ctx* h, const rchfsi_operator* op) {
   if (!h) return RCHFSI_ERR_INVALID_ARG;
   return guarded(h, [&] {
     RC_CHECK(op, RCHFSI_ERR_INVALID_ARG, "operator is NULL");
-    RC_CHECK(op->m == h->p.m, RCHFSI_ERR_INVALID_ARG, "operator m differs from params m");
-    RC_CHECK(op->field == RCHFSI_REAL, RCHFSI_ERR_UNSUPPORTED, "complex Hermitian operators are not implemented");
+    RC_CHECK(op->m == (h->cplx ? h->mc : h->p.m), RCHFSI_ERR_INVALID_ARG, "operator m differs from params m");
+    RC_CHECK((op->field == RCHFSI_COMPLEX) == h->cplx, RCHFSI_ERR_INVALID_ARG,
+             "operator field differs from the handle's field");
     h->has_op = false;
-    if (op->kind == RCHFSI_OP_DENSE) {
+    if (op->kind == RCHFSI_OP_DENSE && h->cplx) {
+      h->fe.reset();
+      set_dense_complex(*h, op);
+    } else if (op->kind == RCHFSI_OP_DENSE) {
       h->fe.reset();
       set_dense(*h, op);
     } else if (op->kind == RCHFSI_OP_FE_CELL) {
@@ -352,11 +568,11 @@ int rchfsi_filter(rchfsi_ctx* h, const double* X, const double* Lambda, const do
     need_op(h);
     RC_CHECK(Yp, RCHFSI_ERR_INVALID_ARG, "Yp is NULL");
     rchfsi_ctx& c = *h;
-    const std::vector<double> lam = host_vec(c, Lambda, c.p.block);
-    load_block(c, X, c.w.X.p);
-    load_block(c, W, c.w.W.p);
-    filter_internal(c, c.w.X.p, lam.data(), c.w.W.p, lmin, lT, lmax, degree, c.w.Y.p, false);
-    store_block(c, c.w.Y.p, Yp);
+    const std::vector<double> lam = lam_any(c, Lambda);
+    load_any(c, X, c.w.X.p);
+    load_any(c, W, c.w.W.p);
+    filter_any(c, c.w.X.p, lam.data(), c.w.W.p, lmin, lT, lmax, degree, c.w.Y.p, false, false);
+    store_any(c, c.w.Y.p, Yp);
     RC_CUDA(cudaStreamSynchronize(c.s));
     return RCHFSI_OK;
   });
@@ -368,9 +584,9 @@ int rchfsi_chfsi_filter(rchfsi_ctx* h, const double* X, double lmin, double lT, 
     need_op(h);
     RC_CHECK(Yp, RCHFSI_ERR_INVALID_ARG, "Yp is NULL");
     rchfsi_ctx& c = *h;
-    load_block(c, X, c.w.X.p);
-    filter_internal(c, c.w.X.p, nullptr, nullptr, lmin, lT, lmax, degree, c.w.Y.p, true);
-    store_block(c, c.w.Y.p, Yp);
+    load_any(c, X, c.w.X.p);
+    filter_any(c, c.w.X.p, nullptr, nullptr, lmin, lT, lmax, degree, c.w.Y.p, true, false);
+    store_any(c, c.w.Y.p, Yp);
     RC_CUDA(cudaStreamSynchronize(c.s));
     return RCHFSI_OK;
   });
@@ -381,13 +597,15 @@ int rchfsi_residual(rchfsi_ctx* h, const double* X, const double* Lambda, double
     need_op(h);
     rchfsi_ctx& c = *h;
     const int64_t m = c.p.m;
-    const int N = c.p.block;
-    load_block(c, X, c.w.X.p);
-    to_device(c, Lambda, c.w.evals.p, N);
+    // a complex block needs only the first N embedded columns
+    const int N = c.cplx ? c.Nc : c.p.block;
+    load_any(c, X, c.w.X.p);
+    const std::vector<double> lam = lam_any(c, Lambda);
+    RC_CUDA(cudaMemcpyAsync(c.w.evals.p, lam.data(), N * sizeof(double), cudaMemcpyHostToDevice, c.s));
     apply_A_f64(c, c.w.X.p, c.w.AX.p, N);
     apply_B_f64(c, c.w.X.p, c.w.BX.p, N);
     resid_form_f64(c.s, m, N, c.w.AX.p, c.w.BX.p, c.w.evals.p, c.w.W.p);
-    store_block(c, c.w.W.p, W);
+    store_any(c, c.w.W.p, W);
     if (rnorm) {
       resid_rel_norms(c.s, m, N, c.w.W.p, c.w.X.p, c.w.rabs.p, c.w.xnrm.p);
       from_device(c, c.w.rabs.p, rnorm, N);
@@ -401,11 +619,15 @@ int rchfsi_rayleigh_ritz(rchfsi_ctx* h, const double* Y, double* X, double* eval
   return guarded(h, [&] {
     need_op(h);
     rchfsi_ctx& c = *h;
-    load_block(c, Y, c.w.Y.p);
+    load_any(c, Y, c.w.Y.p);
     const int rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
     if (rc != RCHFSI_OK) return rc;
-    store_block(c, c.w.X.p, X);
-    from_device(c, c.w.evals.p, evals, c.p.block);
+    if (c.cplx) {
+      std::vector<double> ev = host_vec(c, c.w.evals.p, c.p.block);
+      pair_complex(c, ev);
+    }
+    store_any(c, c.w.X.p, X);
+    from_device(c, c.w.evals.p, evals, c.cplx ? c.Nc : c.p.block);
     RC_CUDA(cudaStreamSynchronize(c.s));
     return RCHFSI_OK;
   });
@@ -416,7 +638,14 @@ int rchfsi_lanczos_bounds(rchfsi_ctx* h, const double* v0, int steps, double* lm
     need_op(h);
     rchfsi_ctx& c = *h;
     double* v = c.w.T1.p;
-    to_device(c, v0, v, c.p.m);
+    if (c.cplx) {
+      // complex start vector (interleaved) -> [v_r; v_i]
+      double* st = c.cstage.ensure(2 * c.mc);
+      to_device(c, v0, st, 2 * c.mc);
+      cplx_deinterleave(c.s, c.mc, st, v, v + c.mc);
+    } else {
+      to_device(c, v0, v, c.p.m);
+    }
     lanczos(c, v, steps, lmax, normA);
     return RCHFSI_OK;
   });
@@ -437,19 +666,27 @@ int rchfsi_solve(rchfsi_ctx* h, double* X_inout, double* evals, double* resid, r
     auto ms_since = [](std::chrono::steady_clock::time_point a) {
       return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
     };
-    load_block(c, X_inout, w.Y.p);
+    load_any(c, X_inout, w.Y.p);
     // bounds: Lanczos from the first column of the initial block (contiguous in column-major)
     double lmax = p.lmax, normA = 1.0;
     lanczos(c, w.Y.p, p.lanczos_steps, p.fixed_bounds ? nullptr : &lmax, &normA);
     RC_CHECK(normA > 0.0 && std::isfinite(normA), RCHFSI_ERR_NUMERIC, "||A|| estimate is not positive");
     auto tr = std::chrono::steady_clock::now();
+    // complex problems: convergence and outputs over the first Nc columns (one per complex pair)
+    const int nev = c.cplx ? c.nevc : p.nev;
+    const int Nout = c.cplx ? c.Nc : N;
+    std::vector<double> ev(N), ra(N), xn(N);
     int rc = rayleigh_ritz(c, w.Y.p, w.X.p, w.AX.p, w.BX.p, w.evals.p);
+    if (rc == RCHFSI_OK && c.cplx) {
+      RC_CUDA(cudaMemcpyAsync(ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      RC_CUDA(cudaStreamSynchronize(c.s));
+      pair_complex(c, ev);
+    }
     t_rr += ms_since(tr);
     int it = 0;
     double best = INFINITY;
     int best_it = 0;
     double maxrel = INFINITY, maxabs = INFINITY;
-    std::vector<double> ev(N), ra(N), xn(N);
     int64_t applies = 0;
     double flops = 0.0;
     while (rc == RCHFSI_OK) {
@@ -464,7 +701,7 @@ int rchfsi_solve(rchfsi_ctx* h, double* X_inout, double* evals, double* resid, r
       maxrel = 0.0;
       maxabs = 0.0;
       bool finite = true;
-      for (int j = 0; j < p.nev; ++j) {
+      for (int j = 0; j < nev; ++j) {
         finite = finite && std::isfinite(ra[j]) && std::isfinite(ev[j]);
         maxrel = std::max(maxrel, ra[j] / (normA * xn[j]));
         maxabs = std::max(maxabs, ra[j]);
@@ -490,23 +727,28 @@ int rchfsi_solve(rchfsi_ctx* h, double* X_inout, double* evals, double* resid, r
       const double lT = p.fixed_bounds ? p.lT : ev[N - 1];
       const double lmx = p.fixed_bounds ? p.lmax : lmax;
       const auto tf = std::chrono::steady_clock::now();
-      filter_internal(c, w.X.p, ev.data(), w.W.p, lmin, lT, lmx, p.degree, w.Y.p,
-                      p.method == RCHFSI_METHOD_CHFSI);
+      filter_any(c, w.X.p, ev.data(), w.W.p, lmin, lT, lmx, p.degree, w.Y.p, p.method == RCHFSI_METHOD_CHFSI,
+                 true);
       t_filter += ms_since(tf);
       applies += c.last_applies;
       flops += c.last_flops;
       tr = std::chrono::steady_clock::now();
       rc = rayleigh_ritz(c, w.Y.p, w.X.p, w.AX.p, w.BX.p, w.evals.p);
+      if (rc == RCHFSI_OK && c.cplx) {
+        RC_CUDA(cudaMemcpyAsync(ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        RC_CUDA(cudaStreamSynchronize(c.s));
+        pair_complex(c, ev);
+      }
       t_rr += ms_since(tr);
       ++it;
     }
-    store_block(c, w.X.p, X_inout);
-    from_device(c, w.evals.p, evals, N);
+    store_any(c, w.X.p, X_inout);
+    from_device(c, w.evals.p, evals, Nout);
+    std::vector<double> rel(Nout);
     if (resid) {
-      std::vector<double> rel(N);
-      for (int j = 0; j < N; ++j) rel[j] = ra[j] / (normA * xn[j]);
+      for (int j = 0; j < Nout; ++j) rel[j] = ra[j] / (normA * xn[j]);
       const auto kind = is_device_pointer(resid) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-      RC_CUDA(cudaMemcpyAsync(resid, rel.data(), N * sizeof(double), kind, c.s));
+      RC_CUDA(cudaMemcpyAsync(resid, rel.data(), Nout * sizeof(double), kind, c.s));
     }
     RC_CUDA(cudaStreamSynchronize(c.s));
     if (st) {

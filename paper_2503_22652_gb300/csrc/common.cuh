@@ -157,6 +157,17 @@ void symmetrize_f64(cudaStream_t s, int n, double* A, int lda);
 int jacobi_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, double tol,
                    int max_sweeps);
 
+// Real embedding of complex Hermitian problems (cplx.cu).
+void cplx_deinterleave(cudaStream_t s, int64_t n, const double* in, double* re, double* im);
+void cplx_embed_block(cudaStream_t s, int64_t m, int64_t N, const double* Xc, double* Xe);
+void cplx_extract_cols(cudaStream_t s, int64_t m, int64_t ncols, const double* Xe, const int* cols, double* Yc);
+void cplx_embed_dense(cudaStream_t s, int64_t m, const double* Ac, double* Ae);
+void cplx_embed_blockdiag(cudaStream_t s, int64_t m, const double* B, double* Be);
+void cplx_dot(cudaStream_t s, int64_t m, const double* Xe, const double* BXe, int cu, int cv, double* out);
+void cplx_axpy(cudaStream_t s, int64_t m, double* Xe, double* AXe, double* BXe, int cu, int cv, double ar,
+               double ai, double scale);
+void cplx_rebuild(cudaStream_t s, int64_t m, int64_t N, const double* src, const int* cols, double* dst);
+
 // Lanczos vector helpers
 void dot_f64(cudaStream_t s, int64_t n, const double* x, const double* y, double* out);
 

@@ -96,20 +96,47 @@ void launch_cells(cudaStream_t s, const FeOp& op, const T* A, int64_t a_stride, 
 
 }  // namespace
 
+// A product Y += alpha * Op X on row-major blocks of the (possibly embedded) problem.  For a complex
+// operator the block's rows [0, mc) hold real parts and [mc, 2 mc) imaginary parts:
+//   Y_r += alpha (Ar X_r - Ai X_i),   Y_i += alpha (Ai X_r + Ar X_i)
+// and the real B acts on each half.
+template <typename T, class F>
+void complex_parts(const FeOp& op, bool useB, const T* X, T* Y, int n, T alpha, F&& one) {
+  if (!op.cplx) {
+    one(op, X, Y, alpha);
+    return;
+  }
+  const int64_t off = op.mc * (int64_t)n;
+  if (useB) {
+    one(op, X, Y, alpha);
+    one(op, X + off, Y + off, alpha);
+    return;
+  }
+  const FeOp& im = *op.imag;
+  one(op, X, Y, alpha);
+  one(im, X + off, Y, -alpha);
+  one(im, X, Y + off, alpha);
+  one(op, X + off, Y + off, alpha);
+}
+
 void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n) {
   RC_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * op.m * n, s));
-  const double* M = useB ? op.B64.p : op.A64.p;
-  const int64_t stride = (useB && op.B_shared) ? 0 : (int64_t)op.nc * op.nc;
-  launch_cells<double, 32>(s, op, M, stride, X, Y, n, 1.0, 0, RCHFSI_KERNEL_FE_CELL_F64);
+  complex_parts<double>(op, useB, X, Y, n, 1.0, [&](const FeOp& o, const double* x, double* y, double al) {
+    const double* M = useB ? op.B64.p : o.A64.p;
+    const int64_t stride = (useB && op.B_shared) ? 0 : (int64_t)op.nc * op.nc;
+    launch_cells<double, 32>(s, o, M, stride, x, y, n, al, 0, RCHFSI_KERNEL_FE_CELL_F64);
+  });
 }
 
 void fe_filter_product_f64(cudaStream_t s, const FeOp& op, const double* Ry, double* Rx, int n, double a,
                            int dmode) {
-  launch_cells<double, 32>(s, op, op.A64.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode, RCHFSI_KERNEL_FE_CELL);
+  complex_parts<double>(op, false, Ry, Rx, n, a, [&](const FeOp& o, const double* x, double* y, double al) {
+    launch_cells<double, 32>(s, o, o.A64.p, (int64_t)o.nc * o.nc, x, y, n, al, dmode, RCHFSI_KERNEL_FE_CELL);
+  });
 }
 
-void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
-                           int dmode) {
+static void fe_product_f32_one(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
+                               int dmode) {
   const size_t na = (size_t)op.n_cells * op.nc * op.nc;
   if (precision == RCHFSI_FP32) {
     if (!op.A32.p) {
@@ -120,6 +147,13 @@ void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float*
     return;
   }
   fe_tc_product(s, op, precision, Ry, Rx, n, a, dmode);
+}
+
+void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
+                           int dmode) {
+  complex_parts<float>(op, false, Ry, Rx, n, a, [&](const FeOp& o, const float* x, float* y, float al) {
+    fe_product_f32_one(s, const_cast<FeOp&>(o), precision, x, y, n, al, dmode);
+  });
 }
 
 void recur_terms_rows_f32(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,

@@ -3,6 +3,8 @@
 // here each kernel gathers a cell's rows of the block, multiplies by the cell matrix and
 // scatter-adds the result.
 #pragma once
+#include <memory>
+
 #include "common.cuh"
 
 namespace rchfsi {
@@ -20,6 +22,12 @@ struct FeOp {
   DevBuf<float> Dinv32;
   DevBuf<uint8_t> imgtf, img16;  // cell matrices packed as swizzled tensor-core operand images
   int* err = nullptr;            // device flag raised when a bounded wait in a kernel runs out
+  // Complex Hermitian operator A = Ar + i Ai acting on the real embedding [x_r; x_i] of length 2 mc:
+  // this object holds Ar (A64) and B, `imag` holds Ai; m = 2 mc, Dinv = [D^-1; D^-1].  Each
+  // complex product is four real cell products on the two row halves of the block.
+  bool cplx = false;
+  int64_t mc = 0;
+  std::unique_ptr<FeOp> imag;
 };
 
 // Y (row-major m x n) = Op X, Op = A or B, FP64.  Y is overwritten.

@@ -49,7 +49,8 @@ struct Job {
 struct Warm {
   int64_t m = 0;
   int N = 0;
-  DevBuf<double> X;  // row-major m x N on the device
+  int field = RCHFSI_REAL;
+  DevBuf<double> X;  // row-major m x N on the device (complex: interleaved)
 };
 
 struct Server {
@@ -84,14 +85,19 @@ void copy_in(std::vector<T>& dst, const T* src, size_t n) {
   }
 }
 
+// Values per entry of the caller's blocks and A: 2 for complex problems (interleaved re, im).
+size_t field_factor(const rchfsi_params& p) { return p.field == RCHFSI_COMPLEX ? 2 : 1; }
+
 size_t estimate_footprint(const rchfsi_operator& op, const rchfsi_params& p) {
-  const size_t m = (size_t)p.m, N = (size_t)p.block;
+  // a complex problem runs as its real embedding of twice the rows and block columns
+  const size_t cf = field_factor(p);
+  const size_t m = (size_t)p.m * cf, N = (size_t)p.block * cf;
   size_t t = 0;
   if (op.kind == RCHFSI_OP_DENSE) {
     t += m * m * 8 * (op.B ? 5 : 4);  // A, (B), A D^-1, D^-1 A, low-precision copy
   } else {
     const size_t na = (size_t)op.n_cells * op.n_c * op.n_c;
-    t += na * 8 * (op.B_cells_shared ? 1 : 2) + na * 4 + (size_t)op.n_cells * op.n_c * 4 + m * 8;
+    t += na * 8 * (op.B_cells_shared ? 1 : 2) * cf + na * 4 * cf + (size_t)op.n_cells * op.n_c * 4 + m * 8;
   }
   t += m * N * 8 * 12 + m * N * 4 * 3 + N * N * 8 * 5;
   return t;
@@ -101,14 +107,15 @@ void run_job(Server& S, Job& j) {
   rchfsi_ctx* h = nullptr;
   int rc = rchfsi_create(&h, &j.params, nullptr);
   if (rc == RCHFSI_OK) rc = rchfsi_set_operator(h, &j.hop.op);
-  const size_t blk = (size_t)j.params.m * j.params.block;
-  std::vector<double> X(blk);
+  const size_t blk = (size_t)j.params.m * j.params.block * field_factor(j.params);
   const double* x0 = j.X0.empty() ? nullptr : j.X0.data();
   Warm* wp = nullptr;
   if (rc == RCHFSI_OK && j.warm_key) {
     std::lock_guard<std::mutex> lk(S.mu);
     auto it = S.warm.find(j.warm_key);
-    if (it != S.warm.end() && it->second->m == j.params.m && it->second->N == j.params.block) wp = it->second.get();
+    if (it != S.warm.end() && it->second->m == j.params.m && it->second->N == j.params.block &&
+        it->second->field == j.params.field)
+      wp = it->second.get();
   }
   DevBuf<double> xdev;
   if (rc == RCHFSI_OK) {
@@ -141,6 +148,7 @@ void run_job(Server& S, Job& j) {
         if (!w) w.reset(new Warm());
         w->m = j.params.m;
         w->N = j.params.block;
+        w->field = j.params.field;
         try {
           w->X.ensure(blk);
           cudaMemcpy(w->X.p, xdev.p, blk * sizeof(double), cudaMemcpyDeviceToDevice);
@@ -239,11 +247,12 @@ int rchfsi_submit(rchfsi_ctx* h, const rchfsi_request* rq, uint64_t* ticket) {
     const rchfsi_operator& op = rq->op;
     const rchfsi_params& p = rq->params;
     if (op.m != p.m || p.m <= 0 || p.block <= 0) return RCHFSI_ERR_INVALID_ARG;
-    const size_t m = (size_t)p.m, blk = m * p.block;
+    const size_t cf = field_factor(p);
+    const size_t m = (size_t)p.m, blk = m * p.block * cf;
     HostOp& ho = job->hop;
     ho.op = op;
     if (op.kind == RCHFSI_OP_DENSE) {
-      copy_in(ho.A, op.A, m * m);
+      copy_in(ho.A, op.A, m * m * cf);
       copy_in(ho.B, op.B, m * m);
       copy_in(ho.A_filter, op.A_filter, m * m);
       copy_in(ho.Dinv, op.Dinv, m);
@@ -257,7 +266,7 @@ int rchfsi_submit(rchfsi_ctx* h, const rchfsi_request* rq, uint64_t* ticket) {
       if (op.n_cells <= 0 || op.n_c <= 0) return RCHFSI_ERR_INVALID_ARG;
       const size_t nd = (size_t)op.n_cells * op.n_c, na = nd * op.n_c;
       copy_in(ho.dofs, op.cell_dofs, nd);
-      copy_in(ho.A_cells, op.A_cells, na);
+      copy_in(ho.A_cells, op.A_cells, na * cf);
       copy_in(ho.B_cells, op.B_cells, op.B_cells_shared ? (size_t)op.n_c * op.n_c : na);
       copy_in(ho.Dinv, op.Dinv, m);
       ho.op.cell_dofs = ho.dofs.data();

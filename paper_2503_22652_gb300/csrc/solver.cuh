@@ -68,6 +68,14 @@ struct rchfsi_ctx {
   double last_flops = 0.0;
   bool is_server = false;
   void* server = nullptr;
+  // complex Hermitian problems run as their real embedding (p holds the embedded sizes 2m, 2N,
+  // 2 nev); the caller-facing sizes are kept here
+  bool cplx = false;
+  int64_t mc = 0;
+  int Nc = 0, nevc = 0;
+  rchfsi::DevBuf<double> cstage;  // complex staging (m x N interleaved)
+  rchfsi::DevBuf<int> ccols;      // embedded columns selected for complex outputs
+  rchfsi::DevBuf<double> cdot;    // complex inner product scratch
   rchfsi::prof::Profiler prof;
 };
 
