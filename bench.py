@@ -45,8 +45,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
     ap.add_argument("--rr", default="emulated", choices=["fp64", "emulated"],
                     help="FP64 products of residual / Rayleigh-Ritz: DFMA or BF16-slice emulation")
-    ap.add_argument("--eig", default="syevd", choices=["syevd", "jacobi"],
-                    help="N x N projected eigensolver: cuSOLVER dsyevd or this library's Jacobi kernel")
+    ap.add_argument("--eig", default="tridiag", choices=["syevd", "jacobi", "tridiag"],
+                    help="N x N projected eigensolver: cuSOLVER dsyevd, or this library's Jacobi or tridiagonal kernels")
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only: no comparisons, no end-to-end run, no CPU baseline (profiling runs)")
     return ap.parse_args()
@@ -238,7 +238,11 @@ def peaks():
 def roofline(prof, solve_ms_total, pk, precision):
     """Roofline entry of the kernel class with the largest device time in the timed region."""
     best = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, r = best
+    return class_roofline(best[0], best[1], solve_ms_total, pk, precision)
+
+
+def class_roofline(name, r, solve_ms_total, pk, precision):
+    """Roofline entry of one kernel class: its algorithmic work over its device time."""
     per_launch_ms = r["ms"] / max(r["launches"], 1)
     hbm = pk.get("hbm_gbs", 6800.0)
     bf16 = pk.get("bf16_tflops_sustained", 1700.0)
@@ -260,7 +264,7 @@ def roofline(prof, solve_ms_total, pk, precision):
                       "peak_source": "measured bf16 sustained (of measured)",
                       "fp64_equivalent_tflops": round(ach / 28.0, 2),
                       "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
-    if name in ("gemm_f64", "filter_simt", "fe_cell_f64"):
+    if name in ("gemm_f64", "filter_simt", "fe_cell_f64", "eig", "small_dense"):
         ach = r["flops"] / (r["ms"] * 1e-3) / 1e12
         peak = 69.8 if name == "filter_simt" else 1.25
         return name, {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
@@ -278,6 +282,7 @@ def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2503_22652_gb300 import Solver
     import paper_2503_22652_gb300.build as B
+    from paper_2503_22652_gb300._lib import KERNEL_CLASSES
     torch.cuda.set_device(local_rank)
     if rank == 0 or world == 1:
         B.build()
@@ -326,8 +331,7 @@ def run_gpu(args, rank, world, local_rank):
         times.append(e0.elapsed_time(e1))
         iters.append(st["iterations"])
         resid.append(st["max_rel_residual"])
-    prof = {k: s.profile_read(k) for k in ("filter_tc", "splitk_reduce", "filter_simt", "gemm_f64", "fe_cell",
-                                           "fe_cell_f64", "gemm_f64_emu")}
+    prof = {k: s.profile_read(k) for k in KERNEL_CLASSES}
     launches = s.profile_read("all")["launches"]
     s.profile(False)
     clocks = clk.stop()
@@ -340,6 +344,7 @@ def run_gpu(args, rank, world, local_rank):
     st_last = st
     pk = peaks()
     kname, roof = roofline(prof, sum(times), pk, args.precision)
+    roof_all = {k: class_roofline(k, v, sum(times), pk, args.precision)[1] for k, v in prof.items() if v["launches"]}
     extras = {}
     if not (args.no_extras or args.quick) and rank == 0:
         extras = comparisons(s, prob, args, torch, dev, stream)
@@ -362,6 +367,8 @@ def run_gpu(args, rank, world, local_rank):
                                       if st_last["t_filter_ms"] > 0 else None),
            "solve_status": st_last["status"],
            "roofline_kernel": kname, "roofline": roof,
+           "roofline_by_class": {k: {kk: v[kk] for kk in ("bound", "achieved", "unit", "frac", "share_of_solve")}
+                                 for k, v in roof_all.items()},
            "kernel_classes_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
            "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e}
     out.update(extras)

@@ -97,12 +97,16 @@ typedef struct rchfsi_params {
                             arithmetic units) or RCHFSI_RR_FP64_EMULATED (FP64-accurate products from
                             exact BF16 slices on the tensor cores) */
   int32_t eig_mode;      /* N x N projected eigenproblem: RCHFSI_EIG_SYEVD (cuSOLVER dsyevd, a library
-                            call) or RCHFSI_EIG_JACOBI (this library's parallel cyclic Jacobi kernel) */
+                            call), RCHFSI_EIG_JACOBI or RCHFSI_EIG_TRIDIAG (this library's kernels) */
 } rchfsi_params;
 
 typedef enum {
   RCHFSI_EIG_SYEVD = 0,  /* divide and conquer (cuSOLVER) */
-  RCHFSI_EIG_JACOBI = 1  /* parallel cyclic Jacobi, one cooperative kernel, tolerance 1e-14 */
+  RCHFSI_EIG_JACOBI = 1, /* parallel cyclic Jacobi, one cooperative kernel, tolerance 1e-14 */
+  RCHFSI_EIG_TRIDIAG = 2 /* this library's Householder tridiagonalisation (one thread-block cluster or
+                            cooperative grid), Sturm bisection and inverse iteration with Gram-Schmidt in
+                            clusters of numerically equal eigenvalues; falls back to RCHFSI_EIG_SYEVD for an
+                            order above 3072 or a cluster of more than 256 equal eigenvalues */
 } rchfsi_eig_mode;
 
 typedef enum {
@@ -158,7 +162,7 @@ typedef struct rchfsi_stats {
 
 /* Fill *p with defaults: nev = 1, block = 1, degree = 20, FP64, R-ChFSI, real, max_iter = 100,
  * min_iter = 0, lanczos_steps = 10, stall_iters = 0, fixed_bounds = 0, tol = 1e-8,
- * rr_mode = RCHFSI_RR_FP64_EMULATED. */
+ * rr_mode = RCHFSI_RR_FP64_EMULATED, eig_mode = RCHFSI_EIG_TRIDIAG. */
 int rchfsi_params_default(rchfsi_params* p);
 
 /* Create a handle on the current CUDA device.  cuda_stream: a cudaStream_t to run on, or NULL
@@ -273,7 +277,12 @@ typedef enum {
   RCHFSI_KERNEL_FE_CELL_F64 = 5,   /* FE cell-matrix product of the residual / Rayleigh-Ritz (FP64) */
   RCHFSI_KERNEL_GEMM_F64_EMU = 6,  /* FP64-accurate GEMM from BF16 slices on the tensor cores; flops are
                                       the tensor-core flops (28 slice products) */
-  RCHFSI_KERNEL_CLASSES = 7
+  RCHFSI_KERNEL_SMALL_DENSE = 7,   /* N x N steps of Rayleigh-Ritz: Cholesky, triangular solves,
+                                      symmetrisation */
+  RCHFSI_KERNEL_EIG = 8,           /* projected N x N eigensolver (syevd library call or Jacobi kernel) */
+  RCHFSI_KERNEL_RR_AUX = 9,        /* m x N passes of Rayleigh-Ritz: column norms and scaling, BF16
+                                      slicing of the emulated GEMM operands */
+  RCHFSI_KERNEL_CLASSES = 10
 } rchfsi_kernel_class;
 
 /* enable = 1: start timing every instrumented launch of this handle with CUDA events on the

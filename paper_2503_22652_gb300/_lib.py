@@ -29,9 +29,9 @@ METHOD_RCHFSI, METHOD_CHFSI = 0, 1
 REAL, COMPLEX = 0, 1
 OP_DENSE, OP_FE_CELL = 0, 1
 KERNEL_CLASSES = {"filter_tc": 0, "splitk_reduce": 1, "filter_simt": 2, "gemm_f64": 3, "fe_cell": 4,
-                  "fe_cell_f64": 5, "gemm_f64_emu": 6}
+                  "fe_cell_f64": 5, "gemm_f64_emu": 6, "small_dense": 7, "eig": 8, "rr_aux": 9}
 RR_MODES = {"fp64": 0, "emulated": 1}
-EIG_MODES = {"syevd": 0, "jacobi": 1}
+EIG_MODES = {"syevd": 0, "jacobi": 1, "tridiag": 2}
 
 dptr = C.POINTER(C.c_double)
 

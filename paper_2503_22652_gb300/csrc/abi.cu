@@ -84,7 +84,7 @@ void validate_params(const rchfsi_params* p) {
            "block larger than 6144 (3072 for complex problems)");
   RC_CHECK(p->rr_mode == RCHFSI_RR_FP64 || p->rr_mode == RCHFSI_RR_FP64_EMULATED, RCHFSI_ERR_INVALID_ARG,
            "bad rr_mode");
-  RC_CHECK(p->eig_mode == RCHFSI_EIG_SYEVD || p->eig_mode == RCHFSI_EIG_JACOBI, RCHFSI_ERR_INVALID_ARG,
+  RC_CHECK(p->eig_mode >= RCHFSI_EIG_SYEVD && p->eig_mode <= RCHFSI_EIG_TRIDIAG, RCHFSI_ERR_INVALID_ARG,
            "bad eig_mode");
 }
 
@@ -456,6 +456,7 @@ int rchfsi_params_default(rchfsi_params* p) {
   p->stall_iters = 0;
   p->fixed_bounds = 0;
   p->rr_mode = RCHFSI_RR_FP64_EMULATED;
+  p->eig_mode = RCHFSI_EIG_TRIDIAG;
   p->tol = 1e-8;
   return RCHFSI_OK;
 }

@@ -27,6 +27,7 @@ void Work::ensure(int64_t m_, int N_) {
   X.ensure(blk); AX.ensure(blk); BX.ensure(blk); W.ensure(blk); Y.ensure(blk); AY.ensure(blk); BY.ensure(blk);
   T1.ensure(blk);
   GA.ensure((size_t)N * N); GB.ensure((size_t)N * N); Z.ensure((size_t)N * N); Zt.ensure((size_t)N * N);
+  Lb.ensure((size_t)N * N); Li.ensure((size_t)N * N);
   evals.ensure(N); nrm.ensure(N); rabs.ensure(N); xnrm.ensure(N);
   info.ensure(4);
   RC_CUDA(cudaMemset(info.p, 0, 4 * sizeof(int)));
@@ -458,7 +459,10 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   const int N = c.p.block;
   Work& w = c.w;
   // column scaling to unit 2-norm (span unchanged)
-  col_norms_f64(c.s, m, N, Y, m, w.nrm.p);
+  {
+    prof::Scope ps(c.s, RCHFSI_KERNEL_RR_AUX, 2.0 * m * N, 8.0 * m * N);
+    col_norms_f64(c.s, m, N, Y, m, w.nrm.p);
+  }
   // invert norms on device: reuse scale kernel through a tiny copy
   {
     std::vector<double> hn(N);
@@ -470,6 +474,7 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
       hn[j] = 1.0 / hn[j];
     }
     RC_CUDA(cudaMemcpyAsync(w.nrm.p, hn.data(), N * sizeof(double), cudaMemcpyHostToDevice, c.s));
+    prof::Scope ps(c.s, RCHFSI_KERNEL_RR_AUX, (double)m * N, 16.0 * m * N);
     scale_cols_f64(c.s, m, N, Y, m, w.nrm.p);
     RC_CUDA(cudaStreamSynchronize(c.s));
   }
@@ -506,31 +511,57 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
     gemm_f64(c.s, N, N, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
     gemm_f64(c.s, N, N, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
   }
-  symmetrize_f64(c.s, N, w.GA.p, N);
-  symmetrize_f64(c.s, N, w.GB.p, N);
-  cholesky_f64(c.s, N, w.GB.p, N, w.info.p);
+  {
+    // G_B = L L^T and L^-1 (one cluster / cooperative kernel)
+    prof::Scope ps(c.s, RCHFSI_KERNEL_SMALL_DENSE, 2.0 * N * N * N / 3.0, 8.0 * N * N * 3);
+    symmetrize_f64(c.s, N, w.GA.p, N);
+    symmetrize_f64(c.s, N, w.GB.p, N);
+    cholesky_inverse_f64(c.s, N, w.GB.p, w.Lb.p, w.Li.p, w.info.p, c.num_sms, w.eigws);
+  }
   int info = 0;
   RC_CUDA(cudaMemcpyAsync(&info, w.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaStreamSynchronize(c.s));
   if (info != 0) return RCHFSI_ERR_ILL_CONDITIONED;
-  // M = L^-1 G_A L^-T
-  trsm_lower_left_f64(c.s, N, N, w.GB.p, N, w.GA.p, N);
-  transpose_f64(c.s, N, N, w.GA.p, N, w.Z.p, N);
-  trsm_lower_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
-  symmetrize_f64(c.s, N, w.Z.p, N);
-  // eigenpairs of the projected matrix (eigenvectors overwrite Z)
-  if (c.p.eig_mode == RCHFSI_EIG_JACOBI) {
-    jacobi_eig_f64(c.s, N, w.Z.p, w.Zt.p, evals, w.syev_work, 1e-14, 60);
-    RC_CUDA(cudaMemcpyAsync(w.Z.p, w.Zt.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));
-  } else {
-    syevd(c, N, w.Z.p, evals);
+  // M = L^-1 G_A L^-T (two FP64 GEMMs on all SMs)
+  {
+    EpiArgs e1 = epi_store(w.Zt.p, N), e2 = epi_store(w.Z.p, N);
+    e1.prof_cls = e2.prof_cls = RCHFSI_KERNEL_SMALL_DENSE;
+    gemm_f64(c.s, N, N, N, w.Li.p, N, false, w.GA.p, N, true, e1);
+    gemm_f64(c.s, N, N, N, w.Zt.p, N, false, w.Li.p, N, false, e2);
+    prof::Scope ps(c.s, RCHFSI_KERNEL_SMALL_DENSE, 0.0, 8.0 * N * N * 2);
+    symmetrize_f64(c.s, N, w.Z.p, N);
+  }
+  // eigenpairs of the projected matrix M (in Z, destroyed); eigenvectors land in `vec`
+  double* vec = w.Z.p;
+  {
+    prof::Scope ps(c.s, RCHFSI_KERNEL_EIG, 4.0 * N * N * N, 8.0 * N * N * 2);
+    if (c.p.eig_mode == RCHFSI_EIG_JACOBI) {
+      jacobi_eig_f64(c.s, N, w.Z.p, w.Zt.p, evals, w.syev_work, 1e-14, 60);
+      vec = w.Zt.p;
+    } else if (c.p.eig_mode == RCHFSI_EIG_TRIDIAG) {
+      // keep a copy of M for the library fallback (a cluster of close eigenvalues too large)
+      RC_CUDA(cudaMemcpyAsync(w.Lb.p, w.Z.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));
+      if (sym_eig_f64(c.s, N, w.Z.p, w.Zt.p, evals, w.eigws, w.info.p + 3, c.num_sms)) {
+        vec = w.Zt.p;
+      } else {
+        RC_CUDA(cudaMemcpyAsync(w.Z.p, w.Lb.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));
+        syevd(c, N, w.Z.p, evals);
+      }
+    } else {
+      syevd(c, N, w.Z.p, evals);
+    }
   }
   // E = L^-T V
-  trsm_lower_trans_left_f64(c.s, N, N, w.GB.p, N, w.Z.p, N);
+  double* Ep = vec == w.Z.p ? w.Zt.p : w.Z.p;
+  {
+    EpiArgs e3 = epi_store(Ep, N);
+    e3.prof_cls = RCHFSI_KERNEL_SMALL_DENSE;
+    gemm_f64(c.s, N, N, N, w.Li.p, N, true, vec, N, true, e3);
+  }
   // X = Y E, AX = AY E, BX = BY E
   if (emu) {
     // E^T as N logical rows (row j = column j of E, contiguous); blocks as m logical rows (dofs)
-    oz_slice(c.s, N, N, w.Z.p, N, 1, w.ozE);
+    oz_slice(c.s, N, N, Ep, N, 1, w.ozE);
     oz_slice(c.s, m, N, Y, 1, m, w.ozL);
     oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, X, m, w.ozws, eflag);
     oz_slice(c.s, m, N, AY, 1, m, w.ozL);
@@ -545,9 +576,9 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
       throw Error(RCHFSI_ERR_TIMEOUT, "a bounded wait in the emulated FP64 GEMM ran out");
     }
   } else {
-    gemm_f64(c.s, m, N, N, Y, m, false, w.Z.p, N, true, epi_store(X, m));
-    gemm_f64(c.s, m, N, N, AY, m, false, w.Z.p, N, true, epi_store(AX, m));
-    gemm_f64(c.s, m, N, N, BY, m, false, w.Z.p, N, true, epi_store(BX, m));
+    gemm_f64(c.s, m, N, N, Y, m, false, Ep, N, true, epi_store(X, m));
+    gemm_f64(c.s, m, N, N, AY, m, false, Ep, N, true, epi_store(AX, m));
+    gemm_f64(c.s, m, N, N, BY, m, false, Ep, N, true, epi_store(BX, m));
   }
   RC_CUDA(cudaMemcpyAsync(&info, w.info.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaStreamSynchronize(c.s));

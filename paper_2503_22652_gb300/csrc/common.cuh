@@ -153,6 +153,14 @@ int cholesky_f64(cudaStream_t s, int n, double* A, int lda, int* d_info);  // lo
 void trsm_lower_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
 void trsm_lower_trans_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
 void symmetrize_f64(cudaStream_t s, int n, double* A, int lda);
+// Cholesky G = L L^T and L^-1 (small_eig.cu): A (n x n, col-major) destroyed; L, Linv lower triangular.
+int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Linv, int* d_info, int num_sms,
+                         DevBuf<double>& scratch);
+// Symmetric eigensolver (small_eig.cu: Householder tridiagonalisation, bisection, inverse iteration):
+// M destroyed; V (column-major eigenvectors) and evals ascending.  Returns false when it declines the
+// problem (order > 3072 or a cluster of close eigenvalues too large for inverse iteration).
+bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, int* d_flag,
+                 int num_sms);
 // Symmetric eigensolver (parallel cyclic Jacobi, jacobi.cu): M destroyed; V, evals ascending.
 int jacobi_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, double tol,
                    int max_sweeps);

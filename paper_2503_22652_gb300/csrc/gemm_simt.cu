@@ -213,11 +213,11 @@ void gemm_dispatch(cudaStream_t s, int64_t M, int64_t N, int64_t K, const T* A, 
   }
   RC_CHECK(cdiv(M, BM) <= 65535u, RCHFSI_ERR_INVALID_ARG, "gemm: M too large for the grid");
   const int64_t tiles = (int64_t)cdiv(N, BN) * cdiv(M, BM);
-  // split K when the output alone cannot fill the GPU (target ~4 CTAs per SM, slices >= 256)
+  // split K when the output alone cannot fill the GPU (target ~4 CTAs per SM, slices >= 2 BK)
   int nsplit = 1;
   const int64_t want = 152 * 4;
-  if (tiles < want && K >= 512) {
-    nsplit = (int)std::min<int64_t>((want + tiles - 1) / tiles, K / 256);
+  if (tiles < want && K >= 4 * BK) {
+    nsplit = (int)std::min<int64_t>((want + tiles - 1) / tiles, K / (2 * BK));
     nsplit = std::max(nsplit, 1);
     nsplit = std::min(nsplit, 64);
   }

@@ -334,6 +334,7 @@ void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs,
   op.Kp = (K + KC - 1) / KC * KC;
   op.sl.ensure((size_t)S * op.Rp * op.Kp);
   op.ex.ensure((size_t)R);
+  prof::Scope ps(s, RCHFSI_KERNEL_RR_AUX, 0.0, 8.0 * R * K + 2.0 * S * op.Rp * op.Kp);
   if (op.Rp > R) RC_CUDA(cudaMemsetAsync(op.sl.p, 0, sizeof(__nv_bfloat16) * S * op.Rp * op.Kp, s));
   if (ks == 1) {
     rowexp_kcontig<<<cdiv(R, 8), 256, 0, s>>>(R, K, X, rs, op.ex.p);

@@ -18,7 +18,8 @@ struct Work {
   int64_t m = 0;
   int N = 0;
   DevBuf<double> X, AX, BX, W, Y, AY, BY, T1;  // m x N
-  DevBuf<double> GA, GB, Z, Zt;                // N x N
+  DevBuf<double> GA, GB, Z, Zt, Lb, Li;        // N x N (Lb: Cholesky factor, Li: its inverse)
+  DevBuf<double> eigws;                        // workspace of the projected eigensolver
   DevBuf<double> evals, nrm, rabs, xnrm, lamtab;
   DevBuf<float> R32a, R32b, W32;               // low-precision filter buffers (col-major or row-major)
   DevBuf<__nv_bfloat16> R16a, R16b, W16;
