@@ -231,6 +231,22 @@ int rchfsi_lanczos_bounds(struct rchfsi_ctx* h, const double* v0, int steps, dou
  * STAGNATED, ILL_CONDITIONED or NUMERIC (X_inout/evals hold the last iterate in every case). */
 int rchfsi_solve(struct rchfsi_ctx* h, double* X_inout, double* evals, double* resid, rchfsi_stats* st);
 
+/* Several independent problems solved together (e.g. the k-points of a Bloch problem): count
+ * distinct handles, each with its operator set; X_inout[i], evals[i], resid[i] (evals / resid may be
+ * NULL, or hold NULL entries), stats[i] (stats may be NULL) are as for rchfsi_solve.  Every problem
+ * runs Algorithm 1 with its own bounds and convergence test, in lockstep outer iterations: the
+ * filters of all unconverged problems with FE operators, R-ChFSI, one TF32/BF16 precision and one
+ * degree run together - per degree step the recurrence terms of each problem and ONE persistent
+ * tensor-core launch over the cells of every problem (up to 64 real products: 16 complex
+ * problems), the degree loop replayed from a CUDA graph, the cell-GEMM column tile chosen by timing
+ * candidates once per shape - and the residual / Rayleigh-Ritz steps of the problems run
+ * concurrently, each on its own handle's stream from its own host thread.  Other problems are
+ * filtered one after the other.  The handles must not be used elsewhere during the call.  Returns
+ * OK when every problem converged, else the status of the first one that did not (each
+ * stats[i].status holds its own). */
+int rchfsi_solve_batch(struct rchfsi_ctx** handles, int count, double** X_inout, double** evals, double** resid,
+                       rchfsi_stats* stats);
+
 /* ---------------------------------------------------------------- serving (request loop) */
 
 /* One eigensolve request for the server: an operator (copied at submit), the solver params, and

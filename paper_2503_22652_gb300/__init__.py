@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (rchfsi_params, rchfsi_operator, rchfsi_stats, rchfsi_request, rchfsi_result,  # noqa: F401
                    PRECISIONS, METHOD_RCHFSI, METHOD_CHFSI, OK, PENDING)
 
-__all__ = ["Solver", "Server", "RChFSIError", "load_library", "ptr"]
+__all__ = ["Solver", "Server", "RChFSIError", "load_library", "ptr", "solve_batch"]
 
 
 class RChFSIError(RuntimeError):
@@ -229,6 +229,40 @@ class Solver:
         stats["status"] = rc
         stats["history"] = hist[: st.iterations + 1].copy()
         return X, ev, res, stats
+
+
+def solve_batch(solvers, X0s, allow_not_converged=False):
+    """rchfsi_solve_batch: solve several problems together (one Solver each, distinct handles).
+    Returns a list of (X, evals, rel_resid, stats_dict) as Solver.solve does."""
+    lib = _lib.load()
+    n = len(solvers)
+    Xs, evs, ress, hists = [], [], [], []
+    sts = (rchfsi_stats * n)()
+    for i, (s, X0) in enumerate(zip(solvers, X0s)):
+        X = X0.copy() if isinstance(X0, np.ndarray) else X0.clone()
+        X = _check_arr(X, (s.m, s.N), "X0", s.dt)
+        Xs.append(X)
+        evs.append(np.empty(s.N))
+        ress.append(np.empty(s.N))
+        hists.append(np.full(s.params.max_iter + 1, np.nan))
+        sts[i].history = hists[-1].ctypes.data
+    hs = (C.c_void_p * n)(*[s.h for s in solvers])
+    xp = (C.c_void_p * n)(*[ptr(X) for X in Xs])
+    ep = (C.c_void_p * n)(*[e.ctypes.data for e in evs])
+    rp = (C.c_void_p * n)(*[r.ctypes.data for r in ress])
+    rc = lib.rchfsi_solve_batch(hs, n, xp, ep, rp, sts)
+    allow = (OK, _lib.ERR_NOT_CONVERGED, _lib.ERR_STAGNATED) if allow_not_converged else (OK,)
+    if rc not in allow:
+        bad = next((i for i in range(n) if sts[i].status != OK), 0)
+        buf = C.create_string_buffer(1024)
+        lib.rchfsi_last_error(solvers[bad].h, buf, 1024)
+        raise RChFSIError(rc, buf.value.decode(errors="replace"))
+    out = []
+    for i in range(n):
+        st = {k: getattr(sts[i], k) for k, _ in rchfsi_stats._fields_ if k != "history"}
+        st["history"] = hists[i][: sts[i].iterations + 1].copy()
+        out.append((Xs[i], evs[i], ress[i], st))
+    return out
 
 
 class Server:

@@ -86,6 +86,8 @@ SIGNATURES = {
     "rchfsi_rayleigh_ritz": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rchfsi_lanczos_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, dptr, dptr]),
     "rchfsi_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(rchfsi_stats)]),
+    "rchfsi_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_void_p), C.POINTER(rchfsi_stats)]),
     "rchfsi_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_uint64]),
     "rchfsi_server_destroy": (C.c_int, [C.c_void_p]),
     "rchfsi_submit": (C.c_int, [C.c_void_p, C.POINTER(rchfsi_request), C.POINTER(C.c_uint64)]),

@@ -3,7 +3,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "solver.cuh"
 
@@ -439,7 +442,325 @@ void resid_form_f64(cudaStream_t s, int64_t m, int64_t n, const double* AX, cons
 }
 }  // namespace rchfsi
 
+namespace {
+
+// State of one rchfsi_solve (Algorithm 1), split into phases so that several problems can be
+// advanced together (rchfsi_solve_batch): begin (initial block, Lanczos bounds, first
+// Rayleigh-Ritz), check (residuals, convergence test, filter bounds), filter, Rayleigh-Ritz, end.
+struct SolveRun {
+  rchfsi_ctx* h;
+  double* X_inout;
+  double* evals;
+  double* resid;
+  rchfsi_stats* st;
+  double* hist;
+  int N = 0, nev = 0, Nout = 0;
+  double lmax = 0.0, normA = 1.0;
+  std::vector<double> ev, ra, xn;
+  int rc = RCHFSI_OK, it = 0, best_it = 0;
+  double best = INFINITY, maxrel = INFINITY, maxabs = INFINITY;
+  int64_t applies = 0;
+  double flops = 0.0, t_filter = 0.0, t_rr = 0.0;
+  double lmin = 0.0, lT = 0.0, lmx = 0.0;  // bounds of the next filter
+  std::chrono::steady_clock::time_point t0;
+  SolveRun(rchfsi_ctx* h_, double* X, double* e, double* r, rchfsi_stats* s)
+      : h(h_), X_inout(X), evals(e), resid(r), st(s), hist(s ? s->history : nullptr) {}
+};
+
+double ms_since(std::chrono::steady_clock::time_point a) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+}
+
+// After a Rayleigh-Ritz step of a complex problem: one Ritz vector per complex pair.
+void pair_after_rr(SolveRun& r) {
+  rchfsi_ctx& c = *r.h;
+  if (r.rc != RCHFSI_OK || !c.cplx) return;
+  RC_CUDA(cudaMemcpyAsync(r.ev.data(), c.w.evals.p, r.N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  pair_complex(c, r.ev);
+}
+
+void run_begin(SolveRun& r) {
+  rchfsi_ctx& c = *r.h;
+  const rchfsi_params& p = c.p;
+  RC_CHECK(r.X_inout, RCHFSI_ERR_INVALID_ARG, "X_inout is NULL");
+  r.t0 = std::chrono::steady_clock::now();
+  r.N = p.block;
+  // complex problems: convergence and outputs over the first Nc columns (one per complex pair)
+  r.nev = c.cplx ? c.nevc : p.nev;
+  r.Nout = c.cplx ? c.Nc : r.N;
+  r.ev.assign(r.N, 0.0);
+  r.ra.assign(r.N, 0.0);
+  r.xn.assign(r.N, 1.0);
+  load_any(c, r.X_inout, c.w.Y.p);
+  // bounds: Lanczos from the first column of the initial block (contiguous in column-major)
+  r.lmax = p.lmax;
+  lanczos(c, c.w.Y.p, p.lanczos_steps, p.fixed_bounds ? nullptr : &r.lmax, &r.normA);
+  RC_CHECK(r.normA > 0.0 && std::isfinite(r.normA), RCHFSI_ERR_NUMERIC, "||A|| estimate is not positive");
+  const auto tr = std::chrono::steady_clock::now();
+  r.rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
+  pair_after_rr(r);
+  r.t_rr += ms_since(tr);
+}
+
+// Residuals and the convergence test; true when another filter + Rayleigh-Ritz pass is needed
+// (the filter bounds are then in r.lmin, r.lT, r.lmx).
+bool run_check(SolveRun& r) {
+  if (r.rc != RCHFSI_OK) return false;
+  rchfsi_ctx& c = *r.h;
+  const rchfsi_params& p = c.p;
+  const int64_t m = p.m;
+  const int N = r.N;
+  Work& w = c.w;
+  const auto tr = std::chrono::steady_clock::now();
+  resid_form_f64(c.s, m, N, w.AX.p, w.BX.p, w.evals.p, w.W.p);
+  resid_rel_norms(c.s, m, N, w.W.p, w.X.p, w.rabs.p, w.xnrm.p);
+  RC_CUDA(cudaMemcpyAsync(r.ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaMemcpyAsync(r.ra.data(), w.rabs.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaMemcpyAsync(r.xn.data(), w.xnrm.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  r.t_rr += ms_since(tr);
+  r.maxrel = 0.0;
+  r.maxabs = 0.0;
+  bool finite = true;
+  for (int j = 0; j < r.nev; ++j) {
+    finite = finite && std::isfinite(r.ra[j]) && std::isfinite(r.ev[j]);
+    r.maxrel = std::max(r.maxrel, r.ra[j] / (r.normA * r.xn[j]));
+    r.maxabs = std::max(r.maxabs, r.ra[j]);
+  }
+  if (r.hist && r.it <= p.max_iter) r.hist[r.it] = r.maxrel;
+  if (!finite) {
+    r.rc = RCHFSI_ERR_NUMERIC;
+    return false;
+  }
+  if (r.maxrel <= p.tol && r.it >= p.min_iter) return false;
+  if (r.it >= p.max_iter) {
+    r.rc = RCHFSI_ERR_NOT_CONVERGED;
+    return false;
+  }
+  if (r.maxrel < 0.5 * r.best) {
+    r.best = r.maxrel;
+    r.best_it = r.it;
+  } else if (p.stall_iters > 0 && r.it - r.best_it >= p.stall_iters) {
+    r.rc = RCHFSI_ERR_STAGNATED;
+    return false;
+  }
+  r.lmin = p.fixed_bounds ? p.lmin : r.ev[0];
+  r.lT = p.fixed_bounds ? p.lT : r.ev[N - 1];
+  r.lmx = p.fixed_bounds ? p.lmax : r.lmax;
+  return true;
+}
+
+void run_filter_single(SolveRun& r) {
+  rchfsi_ctx& c = *r.h;
+  const auto tf = std::chrono::steady_clock::now();
+  filter_any(c, c.w.X.p, r.ev.data(), c.w.W.p, r.lmin, r.lT, r.lmx, c.p.degree, c.w.Y.p,
+             c.p.method == RCHFSI_METHOD_CHFSI, true);
+  r.t_filter += ms_since(tf);
+  r.applies += c.last_applies;
+  r.flops += c.last_flops;
+}
+
+void run_rr(SolveRun& r) {
+  rchfsi_ctx& c = *r.h;
+  const auto tr = std::chrono::steady_clock::now();
+  r.rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
+  pair_after_rr(r);
+  r.t_rr += ms_since(tr);
+  ++r.it;
+}
+
+void run_end(SolveRun& r) {
+  rchfsi_ctx& c = *r.h;
+  store_any(c, c.w.X.p, r.X_inout);
+  from_device(c, c.w.evals.p, r.evals, r.Nout);
+  std::vector<double> rel(r.Nout);
+  if (r.resid) {
+    for (int j = 0; j < r.Nout; ++j) rel[j] = r.ra[j] / (r.normA * r.xn[j]);
+    const auto kind = is_device_pointer(r.resid) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    RC_CUDA(cudaMemcpyAsync(r.resid, rel.data(), r.Nout * sizeof(double), kind, c.s));
+  }
+  RC_CUDA(cudaStreamSynchronize(c.s));
+  if (r.st) {
+    r.st->iterations = r.it;
+    r.st->status = r.rc;
+    r.st->max_rel_residual = r.maxrel;
+    r.st->max_abs_residual = r.maxabs;
+    r.st->lmax = r.lmax;
+    r.st->normA = r.normA;
+    r.st->t_total_ms = ms_since(r.t0);
+    r.st->t_filter_ms = r.t_filter;
+    r.st->t_rr_ms = r.t_rr;
+    r.st->filter_flops = r.flops;
+    r.st->operator_applies = r.applies;
+  }
+}
+
+// Meeting point of the workers of rchfsi_solve_batch before each filter: the last worker to
+// arrive runs the batched filter for every worker that asked for one, then releases all; workers
+// that are done leave the group.
+struct Rendezvous {
+  std::mutex mu;
+  std::condition_variable cv;
+  int expected = 0, arrived = 0, leaving = 0;
+  uint64_t gen = 0;
+  std::vector<int> want;
+  template <class F>
+  void arrive(int id, bool needs_filter, F&& run) {
+    std::unique_lock<std::mutex> lk(mu);
+    if (needs_filter) want.push_back(id);
+    else ++leaving;
+    const uint64_t g = gen;
+    if (++arrived == expected) {
+      std::vector<int> act;
+      act.swap(want);
+      std::sort(act.begin(), act.end());
+      lk.unlock();
+      if (!act.empty()) run(act);
+      lk.lock();
+      expected -= leaving;
+      leaving = 0;
+      arrived = 0;
+      ++gen;
+      cv.notify_all();
+    } else {
+      cv.wait(lk, [&] { return gen != g; });
+    }
+  }
+};
+
+}  // namespace
+
 extern "C" {
+
+int rchfsi_solve_batch(struct rchfsi_ctx** handles, int count, double** X_inout, double** evals, double** resid,
+                       rchfsi_stats* stats) {
+  if (!handles || count < 1 || !X_inout) return RCHFSI_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i] || !X_inout[i]) return RCHFSI_ERR_INVALID_ARG;
+    if (!handles[i]->has_op) return RCHFSI_ERR_NO_OPERATOR;
+    for (int k = 0; k < i; ++k)
+      if (handles[k] == handles[i]) return RCHFSI_ERR_INVALID_ARG;
+  }
+  std::vector<SolveRun> runs;
+  runs.reserve(count);
+  for (int i = 0; i < count; ++i)
+    runs.emplace_back(handles[i], X_inout[i], evals ? evals[i] : nullptr, resid ? resid[i] : nullptr,
+                      stats ? stats + i : nullptr);
+  // one batch stream for the shared filter launches
+  cudaStream_t bs = nullptr;
+  if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return RCHFSI_ERR_CUDA;
+  int num_sms = handles[0]->num_sms;
+  FeBatchPlan plan;
+  Rendezvous rv;
+  rv.expected = count;
+  std::vector<int> rcs(count, RCHFSI_OK);
+  auto fail = [&](int i, const std::exception& e, int code) {
+    handles[i]->err = e.what();
+    runs[i].rc = code;
+  };
+  // the batched filter, run by the last worker to arrive
+  auto batch_filter = [&](const std::vector<int>& act) {
+    std::vector<int> batched, single;
+    const int deg = handles[act[0]]->p.degree, prec = handles[act[0]]->p.precision;
+    for (int i : act)
+      (fe_batchable(*handles[i], deg) && handles[i]->p.precision == prec ? batched : single).push_back(i);
+    if (batched.size() < 2) {
+      single.insert(single.end(), batched.begin(), batched.end());
+      batched.clear();
+    }
+    if (!batched.empty()) {
+      std::vector<FeFilterJob> jobs;
+      for (int i : batched) {
+        rchfsi_ctx& c = *handles[i];
+        jobs.push_back(FeFilterJob{&c, c.w.X.p, runs[i].ev.data(), c.w.W.p, runs[i].lmin, runs[i].lT, runs[i].lmx,
+                                   c.w.Y.p});
+      }
+      const auto tf = std::chrono::steady_clock::now();
+      try {
+        ProfBind pb(handles[batched[0]]);
+        filter_fe_batch(bs, num_sms, jobs, plan);
+        const double ms = ms_since(tf);
+        for (int i : batched) {
+          runs[i].t_filter += ms;
+          runs[i].applies += handles[i]->last_applies;
+          runs[i].flops += handles[i]->last_flops;
+        }
+      } catch (const Error& e) {
+        for (int i : batched) fail(i, e, e.code);
+      } catch (const std::exception& e) {
+        for (int i : batched) fail(i, e, RCHFSI_ERR_CUDA);
+      }
+    }
+    for (int i : single) {
+      try {
+        ProfBind pb(handles[i]);
+        run_filter_single(runs[i]);
+      } catch (const Error& e) {
+        fail(i, e, e.code);
+      } catch (const std::exception& e) {
+        fail(i, e, RCHFSI_ERR_CUDA);
+      }
+    }
+  };
+  auto worker = [&](int i) {
+    SolveRun& r = runs[i];
+    ProfBind pb(handles[i]);
+    bool ok = true;
+    try {
+      run_begin(r);
+    } catch (const Error& e) {
+      fail(i, e, e.code);
+      ok = false;
+    } catch (const std::exception& e) {
+      fail(i, e, RCHFSI_ERR_CUDA);
+      ok = false;
+    }
+    for (;;) {
+      bool more = false;
+      if (ok) {
+        try {
+          more = run_check(r);
+        } catch (const Error& e) {
+          fail(i, e, e.code);
+        } catch (const std::exception& e) {
+          fail(i, e, RCHFSI_ERR_CUDA);
+        }
+      }
+      rv.arrive(i, more, batch_filter);
+      if (!more || r.rc != RCHFSI_OK) break;
+      try {
+        run_rr(r);
+      } catch (const Error& e) {
+        fail(i, e, e.code);
+        break;
+      } catch (const std::exception& e) {
+        fail(i, e, RCHFSI_ERR_CUDA);
+        break;
+      }
+    }
+    try {
+      run_end(r);
+    } catch (const Error& e) {
+      if (r.rc == RCHFSI_OK) fail(i, e, e.code);
+    } catch (const std::exception& e) {
+      if (r.rc == RCHFSI_OK) fail(i, e, RCHFSI_ERR_CUDA);
+    }
+    rcs[i] = r.rc;
+  };
+  {
+    std::vector<std::thread> th;
+    th.reserve(count);
+    for (int i = 0; i < count; ++i) th.emplace_back(worker, i);
+    for (auto& t : th) t.join();
+  }
+  cudaStreamSynchronize(bs);
+  cudaStreamDestroy(bs);
+  for (int i = 0; i < count; ++i)
+    if (rcs[i] != RCHFSI_OK) return rcs[i];
+  return RCHFSI_OK;
+}
+
 
 int rchfsi_params_default(rchfsi_params* p) {
   if (!p) return RCHFSI_ERR_INVALID_ARG;
@@ -655,117 +976,14 @@ int rchfsi_lanczos_bounds(rchfsi_ctx* h, const double* v0, int steps, double* lm
 int rchfsi_solve(rchfsi_ctx* h, double* X_inout, double* evals, double* resid, rchfsi_stats* st) {
   return guarded(h, [&] {
     need_op(h);
-    rchfsi_ctx& c = *h;
-    const rchfsi_params& p = c.p;
-    const int64_t m = p.m;
-    const int N = p.block;
-    Work& w = c.w;
-    RC_CHECK(X_inout, RCHFSI_ERR_INVALID_ARG, "X_inout is NULL");
-    double* hist = st ? st->history : nullptr;
-    const auto t0 = std::chrono::steady_clock::now();
-    double t_filter = 0.0, t_rr = 0.0;
-    auto ms_since = [](std::chrono::steady_clock::time_point a) {
-      return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
-    };
-    load_any(c, X_inout, w.Y.p);
-    // bounds: Lanczos from the first column of the initial block (contiguous in column-major)
-    double lmax = p.lmax, normA = 1.0;
-    lanczos(c, w.Y.p, p.lanczos_steps, p.fixed_bounds ? nullptr : &lmax, &normA);
-    RC_CHECK(normA > 0.0 && std::isfinite(normA), RCHFSI_ERR_NUMERIC, "||A|| estimate is not positive");
-    auto tr = std::chrono::steady_clock::now();
-    // complex problems: convergence and outputs over the first Nc columns (one per complex pair)
-    const int nev = c.cplx ? c.nevc : p.nev;
-    const int Nout = c.cplx ? c.Nc : N;
-    std::vector<double> ev(N), ra(N), xn(N);
-    int rc = rayleigh_ritz(c, w.Y.p, w.X.p, w.AX.p, w.BX.p, w.evals.p);
-    if (rc == RCHFSI_OK && c.cplx) {
-      RC_CUDA(cudaMemcpyAsync(ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      RC_CUDA(cudaStreamSynchronize(c.s));
-      pair_complex(c, ev);
+    SolveRun r(h, X_inout, evals, resid, st);
+    run_begin(r);
+    while (run_check(r)) {
+      run_filter_single(r);
+      run_rr(r);
     }
-    t_rr += ms_since(tr);
-    int it = 0;
-    double best = INFINITY;
-    int best_it = 0;
-    double maxrel = INFINITY, maxabs = INFINITY;
-    int64_t applies = 0;
-    double flops = 0.0;
-    while (rc == RCHFSI_OK) {
-      tr = std::chrono::steady_clock::now();
-      resid_form_f64(c.s, m, N, w.AX.p, w.BX.p, w.evals.p, w.W.p);
-      resid_rel_norms(c.s, m, N, w.W.p, w.X.p, w.rabs.p, w.xnrm.p);
-      RC_CUDA(cudaMemcpyAsync(ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      RC_CUDA(cudaMemcpyAsync(ra.data(), w.rabs.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      RC_CUDA(cudaMemcpyAsync(xn.data(), w.xnrm.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      RC_CUDA(cudaStreamSynchronize(c.s));
-      t_rr += ms_since(tr);
-      maxrel = 0.0;
-      maxabs = 0.0;
-      bool finite = true;
-      for (int j = 0; j < nev; ++j) {
-        finite = finite && std::isfinite(ra[j]) && std::isfinite(ev[j]);
-        maxrel = std::max(maxrel, ra[j] / (normA * xn[j]));
-        maxabs = std::max(maxabs, ra[j]);
-      }
-      if (hist && it <= p.max_iter) hist[it] = maxrel;
-      if (!finite) {
-        rc = RCHFSI_ERR_NUMERIC;
-        break;
-      }
-      if (maxrel <= p.tol && it >= p.min_iter) break;
-      if (it >= p.max_iter) {
-        rc = RCHFSI_ERR_NOT_CONVERGED;
-        break;
-      }
-      if (maxrel < 0.5 * best) {
-        best = maxrel;
-        best_it = it;
-      } else if (p.stall_iters > 0 && it - best_it >= p.stall_iters) {
-        rc = RCHFSI_ERR_STAGNATED;
-        break;
-      }
-      const double lmin = p.fixed_bounds ? p.lmin : ev[0];
-      const double lT = p.fixed_bounds ? p.lT : ev[N - 1];
-      const double lmx = p.fixed_bounds ? p.lmax : lmax;
-      const auto tf = std::chrono::steady_clock::now();
-      filter_any(c, w.X.p, ev.data(), w.W.p, lmin, lT, lmx, p.degree, w.Y.p, p.method == RCHFSI_METHOD_CHFSI,
-                 true);
-      t_filter += ms_since(tf);
-      applies += c.last_applies;
-      flops += c.last_flops;
-      tr = std::chrono::steady_clock::now();
-      rc = rayleigh_ritz(c, w.Y.p, w.X.p, w.AX.p, w.BX.p, w.evals.p);
-      if (rc == RCHFSI_OK && c.cplx) {
-        RC_CUDA(cudaMemcpyAsync(ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-        RC_CUDA(cudaStreamSynchronize(c.s));
-        pair_complex(c, ev);
-      }
-      t_rr += ms_since(tr);
-      ++it;
-    }
-    store_any(c, w.X.p, X_inout);
-    from_device(c, w.evals.p, evals, Nout);
-    std::vector<double> rel(Nout);
-    if (resid) {
-      for (int j = 0; j < Nout; ++j) rel[j] = ra[j] / (normA * xn[j]);
-      const auto kind = is_device_pointer(resid) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-      RC_CUDA(cudaMemcpyAsync(resid, rel.data(), Nout * sizeof(double), kind, c.s));
-    }
-    RC_CUDA(cudaStreamSynchronize(c.s));
-    if (st) {
-      st->iterations = it;
-      st->status = rc;
-      st->max_rel_residual = maxrel;
-      st->max_abs_residual = maxabs;
-      st->lmax = lmax;
-      st->normA = normA;
-      st->t_total_ms = ms_since(t0);
-      st->t_filter_ms = t_filter;
-      st->t_rr_ms = t_rr;
-      st->filter_flops = flops;
-      st->operator_applies = applies;
-    }
-    return rc;
+    run_end(r);
+    return r.rc;
   });
 }
 

@@ -14,6 +14,10 @@
 
 #include "solver.cuh"
 #include "tc_gemm.cuh"
+#include "fe_tc.cuh"
+
+#include <map>
+#include <tuple>
 
 using namespace rchfsi;
 
@@ -432,10 +436,215 @@ void filter_internal(rchfsi_ctx& c, const double* X, const double* lam_host, con
     RC_CUDA(cudaMemsetAsync(c.w.info.p + 2, 0, sizeof(int), c.s));
     throw Error(RCHFSI_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel ran out");
   }
+  // (a complex FE product is four real cell products; the dense embedding already counts 4x)
   const double flops_per = (c.op_kind == RCHFSI_OP_DENSE)
                                ? 2.0 * (double)c.p.m * (double)c.p.m * N
-                               : 2.0 * (double)c.fe->nc * c.fe->nc * (double)c.fe->n_cells * N;
+                               : 2.0 * (double)c.fe->nc * c.fe->nc * (double)c.fe->n_cells * N *
+                                     (c.fe->cplx ? 4.0 : 1.0);
   c.last_flops = flops_per * (double)c.last_applies;
+}
+
+// ------------------------------------------------------------------ batched FE filter
+namespace {
+
+// Column tile of the batched cell-matrix product, picked by timing candidate tiles on the problem's
+// own data (into a scratch output) the first time a shape is met; cached per shape.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int64_t, int>, int> g_tune_cache;
+
+int tune_bn(cudaStream_t s, int num_sms, FeOp& op, int prec, int n, const float* Ry) {
+  const auto key = std::make_tuple(prec, n, op.nc, (int64_t)op.n_cells, op.cplx ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+  }
+  const int bmax = fe_tc_bn_max(prec);
+  const int nr = (n + 15) / 16 * 16;
+  std::vector<int> cand;
+  for (int bn : {32, 48, 64, 96, 128, 160, 208})
+    if (bn <= bmax && bn <= std::max(nr, 32)) cand.push_back(bn);
+  if (cand.empty()) cand.push_back(16);
+  DevBuf<float> scratch;
+  float* out = scratch.ensure((size_t)op.m * n);
+  cudaEvent_t e0, e1;
+  RC_CUDA(cudaEventCreate(&e0));
+  RC_CUDA(cudaEventCreate(&e1));
+  int best = cand[0];
+  float best_ms = 1e30f;
+  for (int bn : cand) {
+    FeTcPart parts[4];
+    const int np = fe_tc_parts(op, Ry, out, n, 1.f, nullptr, 1, bn, parts);
+    fe_tc_batch(s, prec, parts, np, num_sms);  // warm-up
+    RC_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 2; ++r) fe_tc_batch(s, prec, parts, np, num_sms);
+    RC_CUDA(cudaEventRecord(e1, s));
+    RC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return best;
+}
+
+}  // namespace
+
+FeBatchPlan::~FeBatchPlan() {
+  if (exec) cudaGraphExecDestroy(exec);
+}
+
+bool fe_batchable(const rchfsi_ctx& c, int degree) {
+  return c.op_kind == RCHFSI_OP_FE_CELL && c.fe && (c.p.precision == RCHFSI_TF32 || c.p.precision == RCHFSI_BF16) &&
+         c.p.method == RCHFSI_METHOD_RCHFSI && c.p.degree == degree && c.p.degree >= 2;
+}
+
+void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs, FeBatchPlan& plan) {
+  RC_CHECK(!jobs.empty(), RCHFSI_ERR_INVALID_ARG, "empty batch");
+  const int p = jobs[0].c->p.degree;
+  const int prec = jobs[0].c->p.precision;
+  for (auto& j : jobs)
+    RC_CHECK(fe_batchable(*j.c, p) && j.c->p.precision == prec, RCHFSI_ERR_UNSUPPORTED,
+             "batched filter: FE operators, R-ChFSI, one TF32/BF16 precision and degree");
+  const int nj = (int)jobs.size();
+  std::vector<std::vector<double>> tabs(nj), coefs(nj);
+  std::vector<float*> RX(nj), RY(nj), WL(nj);
+  std::vector<int> nn(nj), bn(nj);
+  std::vector<double*> dtab(nj), dcoef(nj);
+  // 1. per problem: scalars, Lambda table and coefficient table on the device, initial blocks
+  for (int q = 0; q < nj; ++q) {
+    FeFilterJob& J = jobs[q];
+    rchfsi_ctx& c = *J.c;
+    check_bounds(J.lmin, J.lT, J.lmax, p);
+    const int n = c.cplx ? c.Nc : c.p.block;  // a complex block is filtered on its first N columns
+    const int64_t m = c.p.m;
+    const size_t blk = (size_t)m * n;
+    nn[q] = n;
+    double e, cc, s1;
+    std::vector<Coef> co;
+    filter_scalars(J.lmin, J.lT, J.lmax, p, e, cc, s1, co);
+    lambda_table(J.lam, n, e, cc, s1, co, tabs[q]);
+    coefs[q].resize(3 * co.size());
+    for (size_t k = 0; k < co.size(); ++k) {
+      coefs[q][3 * k] = co[k].a;
+      coefs[q][3 * k + 1] = co[k].b;
+      coefs[q][3 * k + 2] = co[k].c;
+    }
+    dtab[q] = c.w.lamtab.ensure(tabs[q].size());
+    dcoef[q] = c.w.coefd.ensure(coefs[q].size());
+    RC_CUDA(cudaMemcpyAsync(dtab[q], tabs[q].data(), tabs[q].size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    RC_CUDA(cudaMemcpyAsync(dcoef[q], coefs[q].data(), coefs[q].size() * sizeof(double), cudaMemcpyHostToDevice,
+                            s));
+    RX[q] = c.w.R32a.ensure(blk);
+    RY[q] = c.w.R32b.ensure(blk);
+    WL[q] = c.w.W32.ensure(blk);
+    double* Wr = c.w.stage_out.ensure(blk);
+    transpose_f64(s, n, m, J.W, m, Wr, n);
+    cast_f64_to_f32(s, blk, Wr, RY[q], s1 / e, 0);
+    cast_f64_to_f32(s, blk, Wr, WL[q], 1.0, 0);
+    fill_zero(s, RX[q], blk * sizeof(float));
+    fe_tc_parts_prepare(s, *c.fe, prec);
+  }
+  // 2. column tiles (autotuned once per shape)
+  for (int q = 0; q < nj; ++q) bn[q] = tune_bn(s, num_sms, *jobs[q].c->fe, prec, nn[q], RY[q]);
+  // 3. the degree loop as one CUDA graph: per step, the recurrence terms of every problem and one
+  //    persistent tensor-core launch over every problem's cells (at most 64 parts per launch)
+  std::vector<uintptr_t> key = {(uintptr_t)p, (uintptr_t)prec};
+  for (int q = 0; q < nj; ++q)
+    for (uintptr_t v : {(uintptr_t)jobs[q].c, (uintptr_t)RX[q], (uintptr_t)RY[q], (uintptr_t)WL[q],
+                        (uintptr_t)dtab[q], (uintptr_t)dcoef[q], (uintptr_t)nn[q], (uintptr_t)bn[q]})
+      key.push_back(v);
+  if (!plan.exec || plan.key != key) {
+    if (plan.exec) {
+      cudaGraphExecDestroy(plan.exec);
+      plan.exec = nullptr;
+    }
+    prof::Profiler* saved = prof::current();
+    prof::current() = nullptr;  // no timing events inside a capture
+    int kernels = 0;
+    RC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      std::vector<float*> rx = RX, ry = RY;
+      for (int k = 0; k + 1 < p; ++k) {
+        std::vector<FeTcPart> parts;
+        for (int q = 0; q < nj; ++q) {
+          rchfsi_ctx& c = *jobs[q].c;
+          recur_terms_rows_f32_dev(s, c.p.m, nn[q], ry[q], rx[q], WL[q], dtab[q] + (size_t)(k + 1) * nn[q],
+                                   dcoef[q] + 3 * k);
+          ++kernels;
+          FeTcPart pp[4];
+          const int np = fe_tc_parts(*c.fe, ry[q], rx[q], nn[q], 0.f, dcoef[q] + 3 * k, 1, bn[q], pp);
+          parts.insert(parts.end(), pp, pp + np);
+        }
+        for (size_t o = 0; o < parts.size(); o += 64) {
+          fe_tc_batch(s, prec, parts.data() + o, (int)std::min<size_t>(64, parts.size() - o), num_sms);
+          ++kernels;
+        }
+        std::swap(rx, ry);
+      }
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      prof::current() = saved;
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    RC_CUDA(cudaStreamEndCapture(s, &g));
+    prof::current() = saved;
+    const cudaError_t ie = cudaGraphInstantiate(&plan.exec, g, 0);
+    cudaGraphDestroy(g);
+    RC_CUDA(ie);
+    plan.key = key;
+    plan.kernels = kernels;
+    plan.replays = 0;
+  }
+  {
+    const double fl = [&] {
+      double f = 0.0;
+      for (int q = 0; q < nj; ++q) {
+        const FeOp& op = *jobs[q].c->fe;
+        f += 2.0 * op.nc * op.nc * (double)op.n_cells * nn[q] * (op.cplx ? 4.0 : 1.0) * (p - 1);
+      }
+      return f;
+    }();
+    prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, fl, 0.0);
+    RC_CUDA(cudaGraphLaunch(plan.exec, s));
+  }
+  // launches inside the capture were counted once; count every later replay too
+  if (plan.replays++ > 0) __atomic_add_fetch(&launch_counter(), (int64_t)plan.kernels, __ATOMIC_RELAXED);
+  // 4. per problem: Y = D^-1 R_Y + X Lambda_p, back in FP64 column-major (+ the J half for complex)
+  for (int q = 0; q < nj; ++q) {
+    FeFilterJob& J = jobs[q];
+    rchfsi_ctx& c = *J.c;
+    const int n = nn[q];
+    const int64_t m = c.p.m;
+    const size_t blk = (size_t)m * n;
+    float* ryf = ((p - 1) % 2 == 0) ? RY[q] : RX[q];
+    double* Wr = c.w.stage_out.p;
+    cast_f32_to_f64(s, blk, ryf, Wr);
+    transpose_f64(s, m, n, Wr, n, J.Y, m);
+    reconstruct_f64(s, m, n, J.Y, m, c.fe->Dinv.p, J.X, dtab[q] + (size_t)p * n, J.Y);
+    if (c.cplx) cplx_rebuild(s, c.mc, c.Nc, J.Y, nullptr, J.Y);
+    c.last_applies = p - 1;
+    c.last_flops = 2.0 * c.fe->nc * c.fe->nc * (double)c.fe->n_cells * n * (c.fe->cplx ? 4.0 : 1.0) * (p - 1);
+  }
+  RC_CUDA(cudaStreamSynchronize(s));  // the host tables must outlive their copies
+  for (int q = 0; q < nj; ++q) {
+    rchfsi_ctx& c = *jobs[q].c;
+    int flag = 0;
+    RC_CUDA(cudaMemcpy(&flag, c.w.info.p + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      RC_CUDA(cudaMemset(c.w.info.p + 2, 0, sizeof(int)));
+      throw Error(RCHFSI_ERR_TIMEOUT, "a bounded wait in the batched tensor-core kernel ran out");
+    }
+  }
 }
 
 // ------------------------------------------------------------------ Rayleigh-Ritz (FP64)

@@ -74,6 +74,20 @@ __global__ void recur_rows_kernel(int64_t total, int n, const T* __restrict__ Ry
   }
 }
 
+// Same update with (a, b, c) = coef[0..2] read on the device, so that a captured CUDA graph of the
+// filter loop stays valid when the Chebyshev coefficients change between outer iterations.
+__global__ void recur_rows_dev_kernel(int64_t total, int n, const float* __restrict__ Ry, float* __restrict__ Rx,
+                                      const float* __restrict__ W, const double* __restrict__ lam,
+                                      const double* __restrict__ coef) {
+  const float a = (float)coef[0], b = (float)coef[1], c = (float)coef[2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    float v = b * Ry[e];
+    if (c != 0.f) v += c * Rx[e];
+    if (W) v += a * W[e] * (float)lam[e % n];
+    Rx[e] = v;
+  }
+}
+
 inline unsigned blocks_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -151,6 +165,11 @@ static void fe_product_f32_one(cudaStream_t s, FeOp& op, int precision, const fl
 
 void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
                            int dmode) {
+  if (precision != RCHFSI_FP32) {
+    // tensor cores: the real and imaginary cell products of a complex operator in one launch
+    fe_tc_product(s, op, precision, Ry, Rx, n, a, dmode);
+    return;
+  }
   complex_parts<float>(op, false, Ry, Rx, n, a, [&](const FeOp& o, const float* x, float* y, float al) {
     fe_product_f32_one(s, const_cast<FeOp&>(o), precision, x, y, n, al, dmode);
   });
@@ -160,6 +179,12 @@ void recur_terms_rows_f32(cudaStream_t s, int64_t m, int n, const float* Ry, flo
                           const double* lam, double a, double b, double c) {
   recur_rows_kernel<float><<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, (float)a, (float)b,
                                                              (float)c);
+  RC_LAUNCH();
+}
+
+void recur_terms_rows_f32_dev(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
+                              const double* lam, const double* coef) {
+  recur_rows_dev_kernel<<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, coef);
   RC_LAUNCH();
 }
 

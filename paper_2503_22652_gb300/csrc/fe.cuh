@@ -47,6 +47,9 @@ void fe_filter_product_f64(cudaStream_t s, const FeOp& op, const double* Ry, dou
 // Elementwise recurrence terms for row-major blocks: Rx = b*Ry + c*Rx + a*W*lam[j]
 void recur_terms_rows_f32(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
                           const double* lam, double a, double b, double c);
+// Same with (a, b, c) = coef[0..2] read on the device (capturable in a CUDA graph).
+void recur_terms_rows_f32_dev(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
+                              const double* lam, const double* coef);
 void recur_terms_rows_f64(cudaStream_t s, int64_t m, int n, const double* Ry, double* Rx, const double* W,
                           const double* lam, double a, double b, double c);
 

@@ -17,6 +17,13 @@
 //              buffers, so the next cell's matrix streams in while the current one is in use).
 // The cell-matrix images are built once per operator and precision by a packing kernel.  Every
 // mbarrier wait is bounded; on a timeout the kernel raises the error flag and unwinds.
+//
+// One launch takes a list of "parts" (up to kMaxParts): each part is one real cell-matrix product
+// (its own cells, images, input and output blocks, width n, tile width BN and scalar a), so the four
+// real products of a complex operator, or the products of many problems (a batch of k-points),
+// run as a single persistent launch over the concatenated cell list.  The scalar a may be read
+// from device memory (a coefficient table), so a captured CUDA graph of the filter loop stays valid
+// when the Chebyshev coefficients change.
 #include "fe_tc.cuh"
 #include "prof.cuh"
 #include "tc_ptx.cuh"
@@ -62,19 +69,35 @@ __global__ void pack_cells_kernel(int64_t n_cells, int nc, const double* __restr
   }
 }
 
-struct FeArgs {
-  int64_t n_cells;
-  int nc, n, BN, ntiles;
-  uint32_t tmem_cols;
+constexpr int kMaxParts = 64;
+
+struct FePart {
+  int64_t n_cells, cell_off;  // cells of this part, and their offset in the concatenated list
   const int* dofs;
-  const uint8_t* img;   // packed cell images
+  const uint8_t* img;         // packed cell images
   const float* Ry;
   float* Rx;
   const double* dinv;
-  float a;
-  int dmode;
-  int* err;
+  const double* coef;         // if set, a = sign * *coef (read by the kernel), else a = a_val
+  float a_val, sign;
+  int nc, n, BN, ntiles, dmode, vec;
 };
+
+struct FeBatch {
+  int nparts;
+  int64_t total_cells;
+  uint32_t tmem_cols;
+  int maxBN;
+  int* err;
+  FePart part[kMaxParts];
+};
+
+// Part holding the global cell g (parts are few: a linear scan).
+__device__ __forceinline__ int part_of(const FeBatch& p, int64_t g) {
+  int q = 0;
+  while (q + 1 < p.nparts && g >= p.part[q + 1].cell_off) ++q;
+  return q;
+}
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -87,8 +110,8 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <bool BF16, bool VEC>
-__global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(FeArgs p) {
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constant__ FeBatch p) {
   constexpr int ES = BF16 ? 2 : 4;
   constexpr int KMMA = BF16 ? 16 : 8;
   constexpr uint32_t kFmt = BF16 ? 1u : 2u;
@@ -99,8 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(FeArgs p) {
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int BN = p.BN;
-  const uint32_t b_bytes = (uint32_t)BN * kNCP * ES;  // (128 / per) k-blocks x BN rows x 128 B
+  const uint32_t b_bytes = (uint32_t)p.maxBN * kNCP * ES;  // one operand stage at the widest tile
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA[2] = {smem, smem + kABytes};
   uint8_t* sB[2] = {smem + 2 * kABytes, smem + 2 * kABytes + b_bytes};
@@ -130,148 +152,165 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(FeArgs p) {
     *vabort = 1;
     atomicExch(p.err, 1);
   };
-
   const int64_t G = gridDim.x;
-  const int64_t my_cells = (p.n_cells > (int64_t)blockIdx.x) ? (p.n_cells - 1 - blockIdx.x) / G + 1 : 0;
-  const int64_t items = my_cells * p.ntiles;
 
   if (warp < 4) {
     // ---------------- gather: thread k owns cell-local dof k
     const int k = threadIdx.x;
-    for (int64_t j = 0; j < items; ++j) {
-      const int64_t cl = j / p.ntiles;
-      const int t = (int)(j % p.ntiles);
-      const int64_t cell = blockIdx.x + cl * G;
-      const int bs = (int)(j & 1);
-      if (*vabort || !tc::mbar_wait(&bempty[bs], (uint32_t)((j >> 1) & 1) ^ 1u)) {
-        fail();
-        break;
-      }
-      uint8_t* img = sB[bs];
-      const int n0 = t * BN;
-      int g = -1;
+    int64_t j = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
+      const FePart& P = p.part[part_of(p, g)];
+      const int64_t cell = g - P.cell_off;
+      const int BN = P.BN;
+      int gi = -1;
       float sc = 0.f;
-      if (k < p.nc) {
-        g = p.dofs[cell * p.nc + k];
-        sc = (p.dmode == 1) ? (float)p.dinv[g] : 1.f;
+      if (k < P.nc) {
+        gi = P.dofs[cell * P.nc + k];
+        sc = (P.dmode == 1) ? (float)P.dinv[gi] : 1.f;
       }
-      const float* row = (g >= 0) ? p.Ry + (int64_t)g * p.n : nullptr;
-      for (int nn = 0; nn < BN; nn += 4) {
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        const int col = n0 + nn;
-        if (row) {
-          if (VEC && col + 3 < p.n) {
-            const float4 q = __ldg(reinterpret_cast<const float4*>(row + col));
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-          } else {
+      const float* row = (gi >= 0) ? P.Ry + (int64_t)gi * P.n : nullptr;
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int bs = (int)(j & 1);
+        if (*vabort || !tc::mbar_wait(&bempty[bs], (uint32_t)((j >> 1) & 1) ^ 1u)) {
+          fail();
+          stop = true;
+          break;
+        }
+        uint8_t* img = sB[bs];
+        const int n0 = t * BN;
+        for (int nn = 0; nn < BN; nn += 4) {
+          float v[4] = {0.f, 0.f, 0.f, 0.f};
+          const int col = n0 + nn;
+          if (row) {
+            if (P.vec && col + 3 < P.n) {
+              const float4 q = __ldg(reinterpret_cast<const float4*>(row + col));
+              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (col + u < p.n) v[u] = __ldg(row + col + u);
+              for (int u = 0; u < 4; ++u)
+                if (col + u < P.n) v[u] = __ldg(row + col + u);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float x = v[u] * sc;
+            uint8_t* dst = img + sw_off<ES>(nn + u, k, BN);
+            if (BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(x);
+            else *reinterpret_cast<float*>(dst) = tf32_rna(x);
           }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float x = v[u] * sc;
-          uint8_t* dst = img + sw_off<ES>(nn + u, k, BN);
-          if (BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(x);
-          else *reinterpret_cast<float*>(dst) = tf32_rna(x);
-        }
+        fence_proxy_async();
+        tc::mbar_arrive(&bfull[bs]);
       }
-      fence_proxy_async();
-      tc::mbar_arrive(&bfull[bs]);
     }
   } else if (warp == 4) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = tc::instr_desc(kFmt, kNCP, BN);
-      for (int64_t j = 0; j < items; ++j) {
-        const int64_t cl = j / p.ntiles;
-        const int t = (int)(j % p.ntiles);
-        const int ab = (int)(cl & 1), bs = (int)(j & 1), xb = (int)(j & 1);
-        bool ok = !*vabort;
-        if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl >> 1) & 1));
-        if (ok) ok = tc::mbar_wait(&bfull[bs], (uint32_t)((j >> 1) & 1));
-        if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
-        if (!ok) {
-          fail();
-          break;
-        }
-        tc::tc_fence_after();
-        const uint32_t a_base = tc::smem_u32(sA[ab]);
-        const uint32_t b_base = tc::smem_u32(sB[bs]);
-        const uint32_t d = tmem + (uint32_t)(xb * BN);
-        constexpr int per = kRowBytes / ES;
+      int64_t j = 0, cl = 0;
+      bool stop = false;
+      for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
+        const FePart& P = p.part[part_of(p, g)];
+        const int BN = P.BN;
+        const uint32_t idesc = tc::instr_desc(kFmt, kNCP, BN);
+        const int ab = (int)(cl & 1);
+        for (int t = 0; t < P.ntiles; ++t, ++j) {
+          const int bs = (int)(j & 1), xb = (int)(j & 1);
+          bool ok = !*vabort;
+          if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl >> 1) & 1));
+          if (ok) ok = tc::mbar_wait(&bfull[bs], (uint32_t)((j >> 1) & 1));
+          if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
+          if (!ok) {
+            fail();
+            stop = true;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a_base = tc::smem_u32(sA[ab]);
+          const uint32_t b_base = tc::smem_u32(sB[bs]);
+          const uint32_t d = tmem + (uint32_t)(xb * p.maxBN);
+          constexpr int per = kRowBytes / ES;
 #pragma unroll
-        for (int kk = 0; kk < kNCP / KMMA; ++kk) {
-          const int kel = kk * KMMA;
-          const uint32_t aoff = (uint32_t)(kel / per) * kNCP * kRowBytes + (uint32_t)((kel % per) * ES);
-          const uint32_t boff = (uint32_t)(kel / per) * BN * kRowBytes + (uint32_t)((kel % per) * ES);
-          const uint64_t ad = tc::sw128_desc(a_base + aoff);
-          const uint64_t bd = tc::sw128_desc(b_base + boff);
-          if (BF16) tc::mma_f16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
-          else tc::mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          for (int kk = 0; kk < kNCP / KMMA; ++kk) {
+            const int kel = kk * KMMA;
+            const uint32_t aoff = (uint32_t)(kel / per) * kNCP * kRowBytes + (uint32_t)((kel % per) * ES);
+            const uint32_t boff = (uint32_t)(kel / per) * BN * kRowBytes + (uint32_t)((kel % per) * ES);
+            const uint64_t ad = tc::sw128_desc(a_base + aoff);
+            const uint64_t bd = tc::sw128_desc(b_base + boff);
+            if (BF16) tc::mma_f16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            else tc::mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&bempty[bs]);
+          tc::mma_commit(&accfull[xb]);
+          if (t == P.ntiles - 1) tc::mma_commit(&aempty[ab]);
         }
-        tc::mma_commit(&bempty[bs]);
-        tc::mma_commit(&accfull[xb]);
-        if (t == p.ntiles - 1) tc::mma_commit(&aempty[ab]);
       }
     }
   } else if (warp < 9) {
     // ---------------- epilogue: TMEM -> scatter-add
     const int q = warp & 3;
     const int i = q * 32 + lane;  // cell-local dof of this thread's accumulator row
-    for (int64_t j = 0; j < items; ++j) {
-      const int64_t cl = j / p.ntiles;
-      const int t = (int)(j % p.ntiles);
-      const int64_t cell = blockIdx.x + cl * G;
-      const int xb = (int)(j & 1);
-      bool ok = !*vabort && tc::mbar_wait(&accfull[xb], (uint32_t)((j >> 1) & 1));
-      if (!ok) fail();
-      if (!__all_sync(0xffffffffu, ok && !*vabort)) break;
-      tc::tc_fence_after();
-      int g = -1;
+    int64_t j = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
+      const FePart& P = p.part[part_of(p, g)];
+      const int64_t cell = g - P.cell_off;
+      const int BN = P.BN;
+      const float a = P.sign * (P.coef ? (float)__ldg(P.coef) : P.a_val);
+      int gi = -1;
       float sc = 0.f;
-      if (i < p.nc) {
-        g = p.dofs[cell * p.nc + i];
-        sc = p.a * ((p.dmode == 2) ? (float)p.dinv[g] : 1.f);
+      if (i < P.nc) {
+        gi = P.dofs[cell * P.nc + i];
+        sc = a * ((P.dmode == 2) ? (float)P.dinv[gi] : 1.f);
       }
-      float* out = (g >= 0) ? p.Rx + (int64_t)g * p.n : nullptr;
-      const int n0 = t * BN;
-      const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * BN);
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(lane_addr + c0, v);
-        if (out) {
+      float* out = (gi >= 0) ? P.Rx + (int64_t)gi * P.n : nullptr;
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int xb = (int)(j & 1);
+        bool ok = !*vabort && tc::mbar_wait(&accfull[xb], (uint32_t)((j >> 1) & 1));
+        if (!ok) fail();
+        if (!__all_sync(0xffffffffu, ok && !*vabort)) {
+          stop = true;
+          break;
+        }
+        tc::tc_fence_after();
+        const int n0 = t * BN;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * p.maxBN);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(lane_addr + c0, v);
+          if (out) {
 #pragma unroll
-          for (int u = 0; u < 16; u += 4) {
-            const int col = n0 + c0 + u;
-            if (VEC && col + 3 < p.n) {
-              atomicAdd(reinterpret_cast<float4*>(out + col),
-                        make_float4(sc * v[u], sc * v[u + 1], sc * v[u + 2], sc * v[u + 3]));
-            } else {
+            for (int u = 0; u < 16; u += 4) {
+              const int col = n0 + c0 + u;
+              if (P.vec && col + 3 < P.n) {
+                atomicAdd(reinterpret_cast<float4*>(out + col),
+                          make_float4(sc * v[u], sc * v[u + 1], sc * v[u + 2], sc * v[u + 3]));
+              } else {
 #pragma unroll
-              for (int w = 0; w < 4; ++w)
-                if (col + w < p.n) atomicAdd(out + col + w, sc * v[u + w]);
+                for (int w = 0; w < 4; ++w)
+                  if (col + w < P.n) atomicAdd(out + col + w, sc * v[u + w]);
+              }
             }
           }
         }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&accempty[xb]);
       }
-      tc::tc_fence_before();
-      tc::mbar_arrive(&accempty[xb]);
     }
   } else {
     // ---------------- cell-matrix loader (warp 9, one lane)
     if (lane == 0) {
       int64_t issued = 0, cl = 0;
-      for (; cl < my_cells; ++cl) {
+      for (int64_t g = blockIdx.x; g < p.total_cells; g += G, ++cl) {
         const int ab = (int)(cl & 1);
         if (*vabort || !tc::mbar_wait(&aempty[ab], (uint32_t)((cl >> 1) & 1) ^ 1u)) {
           fail();
           break;
         }
-        const int64_t cell = blockIdx.x + cl * G;
+        const FePart& P = p.part[part_of(p, g)];
+        const int64_t cell = g - P.cell_off;
         tc::mbar_arrive_expect_tx(&afull[ab], kABytes);
-        bulk_g2s(sA[ab], p.img + cell * (int64_t)kABytes, kABytes, &afull[ab]);
+        bulk_g2s(sA[ab], P.img + cell * (int64_t)kABytes, kABytes, &afull[ab]);
         ++issued;
       }
       if (*vabort) {
@@ -290,14 +329,22 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(FeArgs p) {
 
 }  // namespace
 
-void fe_tc_product(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a, int dmode) {
-  RC_CHECK(precision == RCHFSI_TF32 || precision == RCHFSI_BF16, RCHFSI_ERR_INVALID_ARG, "FE tensor path: TF32/BF16");
-  RC_CHECK(op.nc <= kNCP, RCHFSI_ERR_INVALID_ARG, "n_c larger than 128");
-  const bool bf = precision == RCHFSI_BF16;
+namespace {
+
+// Widest column tile (multiple of 16) that keeps two cell-matrix buffers and two operand stages in
+// shared memory and two accumulators in TMEM, split evenly over the block width n.
+int default_bn(int n, bool bf) {
+  const int bn_max = bf ? 208 : 96;
+  const int ntiles = (n + bn_max - 1) / bn_max;
+  int BN = (((n + ntiles - 1) / ntiles) + 15) / 16 * 16;
+  return BN < 16 ? 16 : BN;
+}
+
+const uint8_t* ensure_images(cudaStream_t s, FeOp& op, bool bf) {
   const int ES = bf ? 2 : 4;
   DevBuf<uint8_t>& img = bf ? op.img16 : op.imgtf;
-  const size_t per_cell = (size_t)kNCP * kNCP * ES;
   if (!img.p) {
+    const size_t per_cell = (size_t)kNCP * kNCP * ES;
     img.ensure(per_cell * op.n_cells);
     const int64_t total = op.n_cells * (int64_t)kNCP * kNCP;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
@@ -305,30 +352,99 @@ void fe_tc_product(cudaStream_t s, FeOp& op, int precision, const float* Ry, flo
     else pack_cells_kernel<false><<<blocks, 256, 0, s>>>(op.n_cells, op.nc, op.A64.p, img.p);
     RC_LAUNCH();
   }
-  // column tile: widest multiple of 16 that keeps two matrix buffers + two operand stages in
-  // shared memory (227 KB) and two accumulators in TMEM (512 columns)
-  const int bn_max = bf ? 208 : 96;
-  const int ntiles = (n + bn_max - 1) / bn_max;
-  int BN = (((n + ntiles - 1) / ntiles) + 15) / 16 * 16;
-  if (BN < 16) BN = 16;
+  return img.p;
+}
+
+}  // namespace
+
+int fe_tc_bn_max(int precision) { return precision == RCHFSI_BF16 ? 208 : 96; }
+
+void fe_tc_parts_prepare(cudaStream_t s, FeOp& op, int precision) {
+  const bool bf = precision == RCHFSI_BF16;
+  ensure_images(s, op, bf);
+  if (op.cplx) ensure_images(s, *op.imag, bf);
+}
+
+void fe_tc_batch(cudaStream_t s, int precision, const FeTcPart* parts, int nparts, int num_sms) {
+  RC_CHECK(precision == RCHFSI_TF32 || precision == RCHFSI_BF16, RCHFSI_ERR_INVALID_ARG, "FE tensor path: TF32/BF16");
+  RC_CHECK(nparts >= 1 && nparts <= kMaxParts, RCHFSI_ERR_INVALID_ARG, "FE tensor path: 1..64 parts per launch");
+  const bool bf = precision == RCHFSI_BF16;
+  const int ES = bf ? 2 : 4;
+  FeBatch b{};
+  b.nparts = nparts;
+  b.maxBN = 16;
+  int64_t off = 0;
+  double flops = 0.0, bytes = 0.0;
+  for (int q = 0; q < nparts; ++q) {
+    const FeTcPart& t = parts[q];
+    FeOp& op = *t.op;
+    RC_CHECK(op.nc <= kNCP, RCHFSI_ERR_INVALID_ARG, "n_c larger than 128");
+    RC_CHECK(t.n >= 1, RCHFSI_ERR_INVALID_ARG, "FE tensor path: empty block");
+    FePart& P = b.part[q];
+    P.n_cells = op.n_cells;
+    P.cell_off = off;
+    P.dofs = op.dofs.p;
+    P.img = ensure_images(s, op, bf);
+    P.Ry = t.Ry;
+    P.Rx = t.Rx;
+    P.dinv = op.Dinv.p;
+    P.coef = t.coef;
+    P.a_val = t.a;
+    P.sign = t.sign;
+    P.nc = op.nc;
+    P.n = t.n;
+    P.BN = t.BN > 0 ? t.BN : default_bn(t.n, bf);
+    RC_CHECK(P.BN % 16 == 0 && P.BN >= 16 && P.BN <= fe_tc_bn_max(precision), RCHFSI_ERR_INVALID_ARG,
+             "FE tensor path: tile width must be a multiple of 16 up to the precision's maximum");
+    P.ntiles = (t.n + P.BN - 1) / P.BN;
+    P.dmode = t.dmode;
+    P.vec = (t.n % 4) == 0;
+    b.maxBN = std::max(b.maxBN, P.BN);
+    off += op.n_cells;
+    const double nc = op.nc, C = (double)op.n_cells, rows = (double)(op.cplx ? op.mc : op.m);
+    flops += 2.0 * nc * nc * C * t.n;
+    bytes += 4.0 * 3.0 * rows * t.n + (double)ES * nc * nc * C;
+  }
+  b.total_cells = off;
+  b.err = parts[0].op->err;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(2 * BN)) cols <<= 1;
-  const size_t smem = 2 * per_cell + 2 * (size_t)BN * kNCP * ES + 1024;
+  while (cols < (uint32_t)(2 * b.maxBN)) cols <<= 1;
+  b.tmem_cols = cols;
+  const size_t per_cell = (size_t)kNCP * kNCP * ES;
+  const size_t smem = 2 * per_cell + 2 * (size_t)b.maxBN * kNCP * ES + 1024;
   RC_CHECK(smem <= 232448 - 1024, RCHFSI_ERR_INVALID_ARG, "FE tensor path: shared memory plan too large");
+  auto kern = bf ? fe_tc_kernel<true> : fe_tc_kernel<false>;
+  RC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(b.total_cells, (int64_t)num_sms);
+  prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, flops, bytes);
+  kern<<<grid, kThreads, smem, s>>>(b);
+  RC_LAUNCH();
+}
+
+void fe_tc_product(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a, int dmode) {
   int dev = 0, sms = 152;
   RC_CUDA(cudaGetDevice(&dev));
   RC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  FeArgs p{op.n_cells, op.nc, n, BN, ntiles, cols, op.dofs.p, img.p, Ry, Rx, op.Dinv.p, a, dmode, op.err};
-  const bool vec = (n % 4) == 0;
-  auto kern = bf ? (vec ? fe_tc_kernel<true, true> : fe_tc_kernel<true, false>)
-                 : (vec ? fe_tc_kernel<false, true> : fe_tc_kernel<false, false>);
-  RC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const unsigned grid = (unsigned)std::min<int64_t>(op.n_cells, (int64_t)sms);
-  const double nc = op.nc, C = (double)op.n_cells;
-  prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, 2.0 * nc * nc * C * n,
-                 4.0 * 3.0 * op.m * n + (double)ES * nc * nc * C);
-  kern<<<grid, kThreads, smem, s>>>(p);
-  RC_LAUNCH();
+  FeTcPart parts[4];
+  const int np = fe_tc_parts(op, Ry, Rx, n, a, nullptr, dmode, 0, parts);
+  fe_tc_batch(s, precision, parts, np, sms);
+}
+
+int fe_tc_parts(FeOp& op, const float* Ry, float* Rx, int n, float a, const double* coef, int dmode, int BN,
+                FeTcPart* out) {
+  if (!op.cplx) {
+    out[0] = FeTcPart{&op, Ry, Rx, n, a, coef, 1.f, dmode, BN};
+    return 1;
+  }
+  // complex operator on the real embedding: rows [0, mc) real parts, [mc, 2 mc) imaginary parts
+  //   Y_r += a (Ar X_r - Ai X_i),   Y_i += a (Ai X_r + Ar X_i)
+  const int64_t off = op.mc * (int64_t)n;
+  FeOp& im = *op.imag;
+  out[0] = FeTcPart{&op, Ry, Rx, n, a, coef, 1.f, dmode, BN};
+  out[1] = FeTcPart{&im, Ry + off, Rx, n, a, coef, -1.f, dmode, BN};
+  out[2] = FeTcPart{&im, Ry, Rx + off, n, a, coef, 1.f, dmode, BN};
+  out[3] = FeTcPart{&op, Ry + off, Rx + off, n, a, coef, 1.f, dmode, BN};
+  return 4;
 }
 
 }  // namespace rchfsi

@@ -27,6 +27,7 @@ struct Work {
   DevBuf<int> info;
   DevBuf<double> lz_v, lz_w, lz_vp, lz_t, lz_ab;  // Lanczos vectors and scalars
   DevBuf<double> syev_work;
+  DevBuf<double> coefd;                        // Chebyshev coefficient table of the batched filter
   DevBuf<double> stage_in, stage_out;          // host <-> device staging (row-major)
   OzOperand ozL, ozR, ozE;                     // FP64-emulation slices of the current operands
   DevBuf<double> ozws;                         // split-K partials of the emulated FP64 GEMM
@@ -99,5 +100,26 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
 void lanczos(rchfsi_ctx& c, const double* v0_dev, int k, double* lmax, double* normA);
 
 size_t device_bytes(const rchfsi_ctx& c);
+
+// Batched FE filter (Algorithm 3 for several problems at once): every degree step runs the
+// recurrence terms of each problem and one persistent tensor-core launch over all problems' cells,
+// the whole degree loop replayed from a CUDA graph (re-captured when the set of problems changes).
+struct FeFilterJob {
+  rchfsi_ctx* c;
+  const double* X;    // column-major block (first N columns are filtered; complex: N = Nc)
+  const double* lam;  // host Ritz values (N)
+  const double* W;    // column-major residual block
+  double lmin, lT, lmax;
+  double* Y;          // output, column-major
+};
+struct FeBatchPlan {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> key;
+  int kernels = 0;
+  int64_t replays = 0;
+  ~FeBatchPlan();
+};
+bool fe_batchable(const rchfsi_ctx& c, int degree);
+void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs, FeBatchPlan& plan);
 
 }  // namespace rchfsi
