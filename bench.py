@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "fe"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "fe", "kpoints"])
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
     ap.add_argument("--rr", default="emulated", choices=["fp64", "emulated"],
@@ -60,6 +60,92 @@ def workload_desc(kind, prec):
     return ("FE generalized problem, periodic 16^3 Q4 cells (262,144 dofs), A = 0.5 K + V-mass (8 seeded "
             "wells), B = consistent mass, D^-1 = GLL-lumped inverse, nev=500, block=600, degree=25, "
             "%s filter products, FP64 Rayleigh-Ritz" % prec)
+
+
+# Batched k-point workload: the structure of the 16-k-point configuration (Bloch problems on
+# periodic Q4 meshes of different sizes, complex Hermitian, nev and block per problem) at reduced
+# mesh sizes (6^3..10^3 cells instead of 8^3..20^3, nev 25..200 instead of 100..800): the full sizes
+# need ~470 GB of solver workspace.
+KPOINTS = dict(n_problems=16, seed=7, nmin=6, nmax=10, nev_range=(25, 200), degree=25, tol=1e-8)
+
+
+def kpoint_problems():
+    specs = wl.fe_config4_list(n_problems=KPOINTS["n_problems"], seed=KPOINTS["seed"], nmin=KPOINTS["nmin"],
+                               nmax=KPOINTS["nmax"], nev_range=KPOINTS["nev_range"])
+    out = []
+    for i, sp in enumerate(specs):
+        p = wl.fe_kpoint_problem(sp["n"], sp["kappa"])
+        rng = np.random.default_rng(100 + i)
+        X0 = rng.standard_normal((p["m"], sp["block"])) + 1j * rng.standard_normal((p["m"], sp["block"]))
+        out.append((sp, p, X0))
+    return out
+
+
+def kpoints_desc(prec):
+    return ("16 Bloch k-point problems (complex Hermitian FE, periodic Q4 meshes of 6^3..10^3 cells = "
+            "13,824..64,000 complex dofs, kappa in [-0.5,0.5)^3, nev 25..200, block ceil(1.2 nev/16)*16, "
+            "degree 25, %s cell products), seeds 7 / 100+i" % prec)
+
+
+def kpoints_run(args, torch, dev):
+    """Batched solve of the k-point list vs the same problems solved one after the other."""
+    from paper_2503_22652_gb300 import Solver, solve_batch
+    prec = args.precision if args.precision in ("tf32", "bf16") else "tf32"
+    probs = kpoint_problems()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    solvers, X0 = [], []
+    for sp, p, x0 in probs:
+        s = Solver(p["m"], nev=sp["nev"], block=sp["block"], degree=KPOINTS["degree"], precision=prec,
+                   field="complex", max_iter=300, tol=KPOINTS["tol"], rr_mode=args.rr, eig_mode=args.eig)
+        s.set_fe(T(p["cell_dofs"]), T(p["A_cells"]), T(p["B_cell"]), T(p["Dinv"]))
+        solvers.append(s)
+        X0.append(T(x0))
+
+    def batched():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = solve_batch(solvers, X0)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3, out
+
+    def sequential():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = [s.solve(x) for s, x in zip(solvers, X0)]
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3, out
+
+    batched()  # warm-up: tile tuning, graph capture, workspaces
+    sequential()
+    solvers[0].profile(True)
+    tb, ob = batched()
+    fe = solvers[0].profile_read("fe_cell")
+    launches = solvers[0].profile_read("all")["launches"]
+    solvers[0].profile(False)
+    ts, osq = sequential()
+    worst = max(st["max_rel_residual"] for _, _, _, st in ob)
+    iters = [st["iterations"] for _, _, _, st in ob]
+    flops = sum(st["filter_flops"] for _, _, _, st in ob)
+    filt_ms = max(st["t_filter_ms"] for _, _, _, st in ob)
+    dev_ev = max(float(np.max(np.abs(a[1][:sp["nev"]] - b[1][:sp["nev"]]) / np.maximum(np.abs(b[1][:sp["nev"]]),
+                                                                                         1.0)))
+                 for a, b, (sp, _, _) in zip(ob, osq, probs))
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    roof = None
+    if fe["launches"] and fe["ms"] > 0:
+        ach = fe["bytes"] / (fe["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                "traffic": None, "peak_source": "measured HBM copy (of measured)", "kernel": "fe_tc_kernel (batched)",
+                "per_launch_ms": fe["ms"] / fe["launches"],
+                "tflops": round(fe["flops"] / (fe["ms"] * 1e-3) / 1e12, 2)}
+    for s in solvers:
+        s.close()
+    return {"batched_ms": round(tb, 1), "sequential_ms": round(ts, 1), "speedup": round(ts / tb, 2),
+            "problems": len(probs), "problems_per_s": round(len(probs) / (tb * 1e-3), 2),
+            "iterations": iters, "max_rel_residual": worst, "max_rel_eval_diff_batched_vs_alone": dev_ev,
+            "filter_tflops": round(flops / (filt_ms * 1e-3) / 1e12, 2) if filt_ms > 0 else None,
+            "roofline": roof, "gpu_launches": int(launches), "precision": prec,
+            "workload": kpoints_desc(prec)}
 
 
 def make_problem(kind):
@@ -205,6 +291,8 @@ def oracle_sample(prob, iters=2):
 def run_reference(args, rank):
     if rank != 0:
         return None
+    if args.workload == "kpoints":
+        return {"impl": "reference", "unavailable": "the oracle arm times the dense and FE workloads only"}
     prob = make_problem(args.workload)
     iters_assumed = 10 if args.workload == "dense" else 8
     samples = []
@@ -276,6 +364,27 @@ def class_roofline(name, r, solve_ms_total, pk, precision):
     return name, {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                   "frac": round(ach / hbm, 4), "traffic": None, "peak_source": "measured HBM copy (of measured)",
                   "share_of_solve": round(r["ms"] / solve_ms_total, 4), "per_launch_ms": per_launch_ms}
+
+
+def run_kpoints(args, rank, world, local_rank):
+    """--workload kpoints: one JSON line for the batched k-point solve (replicas under torchrun)."""
+    import torch
+    import paper_2503_22652_gb300.build as B
+    torch.cuda.set_device(local_rank)
+    B.build()
+    dev = torch.device("cuda", local_rank)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    r = kpoints_run(args, torch, dev)
+    clocks = clk.stop()
+    if rank != 0:
+        return None
+    return {"metric": "batched k-point time-to-1e-8 relative residual (16 problems)", "value": r["batched_ms"],
+            "unit": "ms", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": r["batched_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "%s+f64" % r["precision"],
+            "data": "synthetic", "config": {"workload": r["workload"], "parallelism": "single GPU"},
+            "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": clocks, "e2e": None,
+            "cpu_baseline": None, "kpoints": {k: v for k, v in r.items() if k not in ("roofline", "workload")}}
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -489,6 +598,8 @@ def main():
         dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank)
+    elif args.workload == "kpoints":
+        out = run_kpoints(args, rank, world, local_rank)
     else:
         out = run_gpu(args, rank, world, local_rank)
     if out is not None:

@@ -477,7 +477,7 @@ void pair_after_rr(SolveRun& r) {
   if (r.rc != RCHFSI_OK || !c.cplx) return;
   RC_CUDA(cudaMemcpyAsync(r.ev.data(), c.w.evals.p, r.N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaStreamSynchronize(c.s));
-  pair_complex(c, r.ev);
+  if (!c.rr_paired) pair_complex(c, r.ev);
 }
 
 void run_begin(SolveRun& r) {
@@ -513,8 +513,10 @@ bool run_check(SolveRun& r) {
   const int N = r.N;
   Work& w = c.w;
   const auto tr = std::chrono::steady_clock::now();
-  resid_form_f64(c.s, m, N, w.AX.p, w.BX.p, w.evals.p, w.W.p);
-  resid_rel_norms(c.s, m, N, w.W.p, w.X.p, w.rabs.p, w.xnrm.p);
+  // a complex problem's block is [X_s, J X_s]: its residuals are those of the first Nc columns
+  const int Nr = c.cplx ? c.Nc : N;
+  resid_form_f64(c.s, m, Nr, w.AX.p, w.BX.p, w.evals.p, w.W.p);
+  resid_rel_norms(c.s, m, Nr, w.W.p, w.X.p, w.rabs.p, w.xnrm.p);
   RC_CUDA(cudaMemcpyAsync(r.ev.data(), w.evals.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaMemcpyAsync(r.ra.data(), w.rabs.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaMemcpyAsync(r.xn.data(), w.xnrm.p, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -944,7 +946,7 @@ int rchfsi_rayleigh_ritz(rchfsi_ctx* h, const double* Y, double* X, double* eval
     load_any(c, Y, c.w.Y.p);
     const int rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
     if (rc != RCHFSI_OK) return rc;
-    if (c.cplx) {
+    if (c.cplx && !c.rr_paired) {
       std::vector<double> ev = host_vec(c, c.w.evals.p, c.p.block);
       pair_complex(c, ev);
     }

@@ -691,34 +691,52 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   double* BY = w.BY.p;
   const bool emu = c.p.rr_mode == RCHFSI_RR_FP64_EMULATED;
   int* eflag = w.info.p + 2;
+  // A complex problem's block is Y = [Y1, J Y1] (J = multiplication by i) and A, B commute with J:
+  // the operator products are formed on the first Nc columns and completed by J, which halves the
+  // FP64 operator work.
+  const int Na = c.cplx ? c.Nc : N;
+  auto jcomplete = [&](double* Z) {
+    if (c.cplx) cplx_rebuild(c.s, c.mc, c.Nc, Z, nullptr, Z);
+  };
   if (emu) {
     // FP64-accurate products from BF16 slices: Y as N logical rows of length m
-    oz_slice(c.s, N, m, Y, m, 1, w.ozL);
+    oz_slice(c.s, Na, m, Y, m, 1, w.ozL);
     if (c.op_kind == RCHFSI_OP_DENSE) {
       DenseOp& d = c.dense;
       if (d.ozA.R != m) oz_slice(c.s, m, m, d.A.p, m, 1, d.ozA);
       oz_gemm(c.s, c.num_sms, d.ozA, w.ozL, AY, m, w.ozws, eflag);
+      jcomplete(AY);
       if (d.has_B) {
         if (d.ozB.R != m) oz_slice(c.s, m, m, d.B.p, m, 1, d.ozB);
         oz_gemm(c.s, c.num_sms, d.ozB, w.ozL, BY, m, w.ozws, eflag);
+        jcomplete(BY);
       } else {
         RC_CUDA(cudaMemcpyAsync(BY, Y, sizeof(double) * m * N, cudaMemcpyDeviceToDevice, c.s));
       }
     } else {
-      apply_A_f64(c, Y, AY, N);
-      apply_B_f64(c, Y, BY, N);
+      apply_A_f64(c, Y, AY, Na);
+      jcomplete(AY);
+      apply_B_f64(c, Y, BY, Na);
+      jcomplete(BY);
     }
-    // G_A = Y^T A Y, G_B = Y^T B Y
-    oz_slice(c.s, N, m, AY, m, 1, w.ozR);
+    if (Na != N) oz_slice(c.s, N, m, Y, m, 1, w.ozL);  // every column for the Gram matrices
+    // G_A = Y^T A Y, G_B = Y^T B Y (complex: the left N x Na half; the rest follows from J)
+    oz_slice(c.s, Na, m, AY, m, 1, w.ozR);
     oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GA.p, N, w.ozws, eflag);
-    oz_slice(c.s, N, m, BY, m, 1, w.ozR);
+    oz_slice(c.s, Na, m, BY, m, 1, w.ozR);
     oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag);
   } else {
-    apply_A_f64(c, Y, AY, N);
-    apply_B_f64(c, Y, BY, N);
-    // G_A = Y^T A Y, G_B = Y^T B Y  (N x N, column-major)
-    gemm_f64(c.s, N, N, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
-    gemm_f64(c.s, N, N, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
+    apply_A_f64(c, Y, AY, Na);
+    jcomplete(AY);
+    apply_B_f64(c, Y, BY, Na);
+    jcomplete(BY);
+    // G_A = Y^T A Y, G_B = Y^T B Y  (N x Na, column-major)
+    gemm_f64(c.s, N, Na, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
+    gemm_f64(c.s, N, Na, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
+  }
+  if (c.cplx) {
+    cplx_gram_complete(c.s, c.Nc, w.GA.p);
+    cplx_gram_complete(c.s, c.Nc, w.GB.p);
   }
   {
     // G_B = L L^T and L^-1 (one cluster / cooperative kernel)
@@ -767,10 +785,46 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
     e3.prof_cls = RCHFSI_KERNEL_SMALL_DENSE;
     gemm_f64(c.s, N, N, N, w.Li.p, N, true, vec, N, true, e3);
   }
-  // X = Y E, AX = AY E, BX = BY E
+  // X = Y E, AX = AY E, BX = BY E.  Complex problems: each complex Ritz pair appears twice; when
+  // every cluster of equal Ritz values is a pair, the first member of each is kept and only those
+  // Nc columns are rotated, then completed by J ([X_s, J X_s]); otherwise all columns are rotated
+  // and the caller selects (with complex Gram-Schmidt inside larger clusters).
+  int ncol = N;
+  const double* Erot = Ep;
+  c.rr_paired = false;
+  if (c.cplx) {
+    std::vector<double> ev(N);
+    RC_CUDA(cudaMemcpyAsync(ev.data(), evals, N * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    double scale = 1e-300;
+    for (double v : ev) scale = std::max(scale, std::fabs(v));
+    const double thr = 1e-9 * scale;
+    std::vector<int> sel;
+    bool pairs = true;
+    for (int k = 0; k < N && pairs;) {
+      int e = k + 1;
+      while (e < N && std::fabs(ev[e] - ev[k]) <= thr) ++e;
+      if (e - k == 2) sel.push_back(k);
+      else pairs = false;
+      k = e;
+    }
+    if (pairs && (int)sel.size() == c.Nc) {
+      int* dcols = c.ccols.ensure(c.Nc);
+      RC_CUDA(cudaMemcpyAsync(dcols, sel.data(), sizeof(int) * c.Nc, cudaMemcpyHostToDevice, c.s));
+      double* Es = (Ep == w.Z.p) ? w.Zt.p : w.Z.p;  // the eigenvectors V are no longer needed
+      gather_cols_f64(c.s, N, c.Nc, Ep, dcols, Es);
+      std::vector<double> e2(N);
+      for (int j = 0; j < c.Nc; ++j) e2[j] = e2[c.Nc + j] = ev[sel[j]];
+      RC_CUDA(cudaMemcpyAsync(evals, e2.data(), N * sizeof(double), cudaMemcpyHostToDevice, c.s));
+      RC_CUDA(cudaStreamSynchronize(c.s));  // sel and e2 must outlive their copies
+      ncol = c.Nc;
+      Erot = Es;
+      c.rr_paired = true;
+    }
+  }
   if (emu) {
-    // E^T as N logical rows (row j = column j of E, contiguous); blocks as m logical rows (dofs)
-    oz_slice(c.s, N, N, Ep, N, 1, w.ozE);
+    // E^T as ncol logical rows (row j = column j of E, contiguous); blocks as m logical rows (dofs)
+    oz_slice(c.s, ncol, N, Erot, N, 1, w.ozE);
     oz_slice(c.s, m, N, Y, 1, m, w.ozL);
     oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, X, m, w.ozws, eflag);
     oz_slice(c.s, m, N, AY, 1, m, w.ozL);
@@ -785,9 +839,14 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
       throw Error(RCHFSI_ERR_TIMEOUT, "a bounded wait in the emulated FP64 GEMM ran out");
     }
   } else {
-    gemm_f64(c.s, m, N, N, Y, m, false, Ep, N, true, epi_store(X, m));
-    gemm_f64(c.s, m, N, N, AY, m, false, Ep, N, true, epi_store(AX, m));
-    gemm_f64(c.s, m, N, N, BY, m, false, Ep, N, true, epi_store(BX, m));
+    gemm_f64(c.s, m, ncol, N, Y, m, false, Erot, N, true, epi_store(X, m));
+    gemm_f64(c.s, m, ncol, N, AY, m, false, Erot, N, true, epi_store(AX, m));
+    gemm_f64(c.s, m, ncol, N, BY, m, false, Erot, N, true, epi_store(BX, m));
+  }
+  if (c.rr_paired) {
+    jcomplete(X);
+    jcomplete(AX);
+    jcomplete(BX);
   }
   RC_CUDA(cudaMemcpyAsync(&info, w.info.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   RC_CUDA(cudaStreamSynchronize(c.s));

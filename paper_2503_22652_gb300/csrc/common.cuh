@@ -175,6 +175,8 @@ void cplx_dot(cudaStream_t s, int64_t m, const double* Xe, const double* BXe, in
 void cplx_axpy(cudaStream_t s, int64_t m, double* Xe, double* AXe, double* BXe, int cu, int cv, double ar,
                double ai, double scale);
 void cplx_rebuild(cudaStream_t s, int64_t m, int64_t N, const double* src, const int* cols, double* dst);
+void cplx_gram_complete(cudaStream_t s, int64_t N, double* G);  // right half of [[P, Q], [-Q, P]] (2N x 2N)
+void gather_cols_f64(cudaStream_t s, int64_t rows, int64_t ncols, const double* src, const int* cols, double* dst);
 
 // Lanczos vector helpers
 void dot_f64(cudaStream_t s, int64_t n, const double* x, const double* y, double* out);

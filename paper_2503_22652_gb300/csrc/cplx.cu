@@ -151,7 +151,37 @@ __global__ void rebuild_kernel(int64_t m, int64_t N, const double* src, const in
   }
 }
 
+// Gram matrix of an embedded block Y = [Y1, J Y1] (2N x 2N, column-major) from its left half:
+// G = [[P, Q], [-Q, P]], so G(i, N + j) = -G(N + i, j) for i < N and G(i - N, j) for i >= N.
+__global__ void gram_complete_kernel(int64_t N, double* G) {
+  const int64_t n2 = 2 * N, total = n2 * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n2, i = e - j * n2;
+    G[(N + j) * n2 + i] = i < N ? -G[j * n2 + N + i] : G[j * n2 + i - N];
+  }
+}
+
+// dst(:, j) = src(:, cols[j]) for column-major blocks with `rows` rows.
+__global__ void gather_cols_kernel(int64_t rows, int64_t ncols, const double* __restrict__ src,
+                                   const int* __restrict__ cols, double* __restrict__ dst) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / rows, i = e - j * rows;
+    dst[e] = src[(int64_t)cols[j] * rows + i];
+  }
+}
+
 }  // namespace
+
+void cplx_gram_complete(cudaStream_t s, int64_t N, double* G) {
+  gram_complete_kernel<<<blocks_for(2 * N * N), 256, 0, s>>>(N, G);
+  RC_LAUNCH();
+}
+
+void gather_cols_f64(cudaStream_t s, int64_t rows, int64_t ncols, const double* src, const int* cols, double* dst) {
+  gather_cols_kernel<<<blocks_for(rows * ncols), 256, 0, s>>>(rows, ncols, src, cols, dst);
+  RC_LAUNCH();
+}
 
 void cplx_deinterleave(cudaStream_t s, int64_t n, const double* in, double* re, double* im) {
   deinterleave_kernel<<<blocks_for(n), 256, 0, s>>>(n, in, re, im);

@@ -31,10 +31,38 @@ constexpr uint32_t kBBytes = S * BN * 128;   // 28 KB: all B slices of one chunk
 constexpr uint32_t kTmemCols = 512;          // 2 buffers x 7 levels x 32 columns = 448
 
 // ---------------------------------------------------------------- slicing
+// FP64 arithmetic is scarce on this GPU, so the slicing works on the bits: the binary exponent E
+// with |x| in [2^(E-1), 2^E) (E = -100000 for 0), and the digits of x 2^(56 - e) in base 256 by
+// integer shifts.
 __device__ __forceinline__ int exp_of(double x) {
-  int e = 0;
-  if (x != 0.0) frexp(x, &e);
-  return x != 0.0 ? e : -100000;
+  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  if (b == 0) return -100000;
+  const int eb = (int)(b >> 52);
+  if (eb != 0) return eb - 1022;
+  // subnormal: 2^-1074 times the 52-bit fraction
+  return -1074 + (64 - __clzll(b));
+}
+
+// round(x 2^(56 - e)) as a signed 64-bit integer, for |x| < 2^e (so |result| <= 2^56).
+__device__ __forceinline__ long long fixed56(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const long long b = bits & 0x7fffffffffffffffLL;
+  if (b == 0) return 0;
+  const int eb = (int)(b >> 52);
+  long long mant = b & 0x000fffffffffffffLL;
+  int ex;  // x = mant 2^ex
+  if (eb != 0) {
+    mant |= 0x0010000000000000LL;
+    ex = eb - 1075;
+  } else {
+    ex = -1074;
+  }
+  const int sh = ex + 56 - e;  // <= 4 since |x| < 2^e
+  long long f;
+  if (sh >= 0) f = mant << sh;
+  else if (sh > -63) f = (mant + (1LL << (-sh - 1))) >> (-sh);
+  else f = 0;
+  return bits < 0 ? -f : f;
 }
 
 // Row exponents, K-contiguous rows: one warp per row.
@@ -80,15 +108,21 @@ __global__ void slice_kernel(int64_t R, int64_t Rp, int64_t K, int64_t Kp, const
     const int64_t r = r0 + rr;
     if (r >= R) continue;
     const int e = ex[r];
+    // digits t_s of x 2^(-e) = sum_s t_s 2^(-8(s+1)), rounded to nearest: |t_0| <= 256, |t_s| <= 128,
+    // each exact in BF16; two neighbouring k per thread, stored as one 4-byte pair per slice
+    long long f0 = fixed56(tile[rr][2 * tx], e), f1 = fixed56(tile[rr][2 * tx + 1], e);
+    __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out + (int64_t)r * Kp + k0 + 2 * tx);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int kk = 2 * tx + h;
-      double v = ldexp(tile[rr][kk], -e);
-      for (int s = 0; s < S; ++s) {
-        const double t = rint(v * 256.0);
-        v = v * 256.0 - t;
-        out[((int64_t)s * Rp + r) * Kp + k0 + kk] = __float2bfloat16_rn((float)t);
+    for (int s = 0; s < S; ++s) {
+      const int sh = 48 - 8 * s;
+      long long t0 = f0, t1 = f1;
+      if (sh > 0) {
+        t0 = (f0 + (1LL << (sh - 1))) >> sh;
+        t1 = (f1 + (1LL << (sh - 1))) >> sh;
+        f0 -= t0 << sh;
+        f1 -= t1 << sh;
       }
+      o2[(int64_t)s * Rp * Kp / 2] = __floats2bfloat162_rn((float)t0, (float)t1);
     }
   }
 }

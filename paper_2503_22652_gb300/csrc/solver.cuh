@@ -78,6 +78,7 @@ struct rchfsi_ctx {
   rchfsi::DevBuf<double> cstage;  // complex staging (m x N interleaved)
   rchfsi::DevBuf<int> ccols;      // embedded columns selected for complex outputs
   rchfsi::DevBuf<double> cdot;    // complex inner product scratch
+  bool rr_paired = false;         // the last Rayleigh-Ritz already kept one Ritz vector per complex pair
   rchfsi::prof::Profiler prof;
 };
 
