@@ -4,9 +4,9 @@
 // 64-wide K chunk, the 7 B slices of the tile (one 28 KB stage, two stages) and the 7 A slices
 // (16 KB each, a 6-deep ring) with TMA; warp 1 (one lane) issues, for each A slice s, the products
 // with B slices t <= 6 - s (4 x tcgen05.mma kind::f16, K = 16) into the TMEM accumulator of level
-// s + t (7 levels x 32 columns, two buffers = 448 columns); warps 4-11 (two per TMEM lane quarter,
-// 16 columns each) drain a finished chunk: tcgen05.ld of the 7 levels, exact scaling by 2^-8L and
-// TwoSum into per-output float-float accumulators.  The final value (hi + lo) 2^(e_i + f_j - 16) is
+// s + t (7 levels x 32 columns, two buffers = 448 columns), accumulating GROUP chunks per buffer;
+// warps 4-11 (two per TMEM lane quarter, 16 columns each) drain a finished group: tcgen05.ld of the
+// 7 levels, exact scaling by 2^-8L and TwoSum into per-output float-float accumulators.  The final value (hi + lo) 2^(e_i + f_j - 16) is
 // stored in FP64 (or, with split-K, written as a partial and summed by a second kernel).
 #include <cudaTypedefs.h>
 
@@ -24,6 +24,9 @@ constexpr int S = kOzSlices;
 constexpr int BM = 128;
 constexpr int BN = 32;
 constexpr int KC = 64;            // K chunk: one 128-byte row of BF16
+// Chunks accumulated in TMEM before a drain: 2 x 64 = 128 K terms per exact FP32 sum (each term a
+// product of two integer slices, |t_s t_r| <= 2^16, so every partial sum stays below 2^23).
+constexpr int GROUP = 2;
 constexpr int ASTAGES = 6;
 constexpr int kThreads = 384;     // 12 warps
 constexpr uint32_t kABytes = BM * 128;       // 16 KB per A slice tile
@@ -229,14 +232,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = tc::instr_desc(1u, BM, BN);  // BF16 x BF16 -> FP32, M = 128, N = 32
       for (int ci = 0; ci < nch; ++ci) {
         const int b = ci & 1;
+        const int g = ci / GROUP, xb = g & 1;  // accumulation group and its TMEM buffer
+        const bool first = (ci % GROUP) == 0, last = (ci % GROUP) == GROUP - 1 || ci == nch - 1;
         bool ok = !*vabort && tc::mbar_wait(&bfull[b], (uint32_t)((ci >> 1) & 1));
-        if (ok) ok = tc::mbar_wait(&accempty[b], (uint32_t)((ci >> 1) & 1) ^ 1u);
+        if (ok && first) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((g >> 1) & 1) ^ 1u);
         if (!ok) {
           fail();
           break;
         }
         const uint32_t b_base = tc::smem_u32(sB + (size_t)b * kBBytes);
-        const uint32_t d_base = tmem + (uint32_t)(b * S * BN);
+        const uint32_t d_base = tmem + (uint32_t)(xb * S * BN);
         for (int s = 0; s < S; ++s) {
           const int j = ci * S + s;
           const int q = j % ASTAGES;
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t ad = tc::sw128_desc(a_base + kk * 32);
               const uint64_t bd = tc::sw128_desc(b_base + (uint32_t)(t * BN * 128) + kk * 32);
-              tc::mma_f16(d, ad, bd, idesc, (s == 0 && kk == 0) ? 0u : 1u);
+              tc::mma_f16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
             }
           }
           tc::mma_commit(&aempty[q]);
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc::mma_commit(&bempty[b]);
-        tc::mma_commit(&accfull[b]);
+        if (last) tc::mma_commit(&accfull[xb]);
       }
     }
   } else if (warp >= 4) {
@@ -272,9 +277,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int u = 0; u < 16; ++u) hi[u] = lo[u] = 0.f;
     bool ok = true;
-    for (int ci = 0; ci < nch; ++ci) {
-      const int b = ci & 1;
-      bool w = !*vabort && tc::mbar_wait(&accfull[b], (uint32_t)((ci >> 1) & 1));
+    const int ngroups = (nch + GROUP - 1) / GROUP;
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      bool w = !*vabort && tc::mbar_wait(&accfull[b], (uint32_t)((g >> 1) & 1));
       if (!w) fail();
       if (!__all_sync(0xffffffffu, w && !*vabort)) {
         ok = false;

@@ -7,9 +7,11 @@
 //     exactly into S = 7 slices of integers |t| <= 256 (bf16-exact): x = 2^e_r sum_s t_s 2^-8(s+1)
 //     + O(2^(e_r - 56));
 //   * C(i,j) = sum_k A(i,k) B(j,k) is assembled from the slice products A_s B_t^T with s + t <= S-1
-//     (28 products), grouped by level L = s + t.  Over one 64-wide K chunk every level's sum is an
-//     integer below 2^24, so the FP32 tensor-core accumulation of that chunk is exact;
-//   * each chunk's levels are combined as sum_L D_L 2^-8L into a float-float (hi, lo) accumulator
+//     (28 products), grouped by level L = s + t.  |t_0| <= 256 and |t_s| <= 128 for s > 0, so over a
+//     group of 128 K terms the sum of level L is an integer below 2^24 for L <= 5 and the FP32
+//     tensor-core accumulation of those levels is exact; the last level (weight 2^-48) could in the
+//     worst case lose one unit, an error below 2^-72 of the product, far under FP64 rounding;
+//   * each group's levels are combined as sum_L D_L 2^-8L into a float-float (hi, lo) accumulator
 //     (TwoSum), and C(i,j) = 2^(e_i + f_j - 16) (hi + lo) is formed in FP64 at the end.
 // The result carries ~2^-48 relative rounding per chunk combination, comparable to an FP64 GEMM's
 // own rounding for the shapes used here.
