@@ -118,3 +118,47 @@ def test_dense_generalized_small_bruteforce():
     np.testing.assert_allclose(r3["eps"][:12], ref[:12], atol=1e-9 * np.abs(ref).max())
     r2 = solver.solve(A, B, X0, 12, 12, 1e-10, 40, lmax, nA, Dinv=D, method="chfsi")
     assert r2["history_rel"][-1] > 1e-8
+
+
+def test_convergence_condition_diagnostic_oracle():
+    """Section 4.1.4 (Eq. 5) on the oracle, zeta = 1e-3: the filtering error of ChFSI saturates at
+    O(zeta) and the condition |C_p(l_n)| - |C_p(l_n+1)| > ||Delta^_p|| (sec + csc) fails, while for
+    R-ChFSI the filtering error decays to round-off and the condition holds."""
+    import scipy.linalg as sla
+    from oracle import chebyshev, filters, rr
+    zeta, n, iters, p = 1e-3, 10, 30, 8
+    t = wl.toy_generalized(zeta)
+    ex = wl.toy_generalized(0.0)
+    A, B = t["A"], t["B"]
+    m = A.shape[0]
+    bounds = (t["lmin"], t["lT"], t["lmax"])
+    lam_all, V = sla.eigh(A, B)
+    L = np.linalg.cholesky(B)
+    Qq = np.linalg.qr(L.T @ V[:, :n])[0]
+    Bh = sla.sqrtm(B).real
+    cp = np.abs(chebyshev.scaled_cheb(p, np.array([lam_all[n - 1], lam_all[n]]), *bounds))
+    lhs = cp[0] - cp[1]
+    Da, De = t["Dinv_dense"], ex["Dinv_dense"]
+    res = {}
+    for method in ("rchfsi", "chfsi"):
+        X, lam, AX, BX = rr.rayleigh_ritz(wl.gaussian_block(m, n, seed=2), lambda v: A @ v, lambda v: B @ v)
+        errs, rhs = [], []
+        for _ in range(iters):
+            W = AX - BX * lam[None, :]
+            if method == "rchfsi":
+                Ya = filters.rchfsi_filter(lambda R: A @ (Da @ R), lambda R: Da @ R, X, lam, W, *bounds, p)
+                Ye = filters.rchfsi_filter(lambda R: A @ (De @ R), lambda R: De @ R, X, lam, W, *bounds, p)
+            else:
+                Ya = filters.chfsi_filter(lambda Y: Da @ (A @ Y), X, *bounds, p)
+                Ye = filters.chfsi_filter(lambda Y: De @ (A @ Y), X, *bounds, p)
+            d = np.linalg.norm(Bh @ (Ya - Ye), 2) / np.linalg.norm(Bh @ Ye, 2)
+            s = np.linalg.svd(Qq.T @ np.linalg.qr(L.T @ X)[0], compute_uv=False).min()
+            th = float(np.arccos(np.clip(s, -1.0, 1.0)))
+            errs.append(d)
+            rhs.append(d * (1.0 / np.cos(th) + 1.0 / max(np.sin(th), 1e-300)))
+            X, lam, AX, BX = rr.rayleigh_ritz(Ya, lambda v: A @ v, lambda v: B @ v)
+        res[method] = (np.array(errs), np.array(rhs))
+    e3, r3 = res["rchfsi"]
+    e2, r2 = res["chfsi"]
+    assert e3[-1] < 1e-12 and e2[-1] > 1e-6
+    assert np.all(r3[5:] < lhs) and r2[-1] > lhs
