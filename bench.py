@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "fe", "kpoints"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "fe", "kpoints", "serving"])
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
     ap.add_argument("--rr", default="emulated", choices=["fp64", "emulated"],
@@ -146,6 +146,118 @@ def kpoints_run(args, torch, dev):
             "filter_tflops": round(flops / (filt_ms * 1e-3) / 1e12, 2) if filt_ms > 0 else None,
             "roofline": roof, "gpu_launches": int(launches), "precision": prec,
             "workload": kpoints_desc(prec)}
+
+
+# Serving stream: Poisson arrivals of requests from four outer-loop chains (real FE meshes of 6^3 and
+# 8^3 cells, complex k-point meshes of 6^3 and 8^3 cells), each request a 1% drift of the well depths
+# of the chain's previous operator, warm-started from the chain's last subspace kept on the device;
+# arrival rate 0.8 x the measured warm single-stream solve rate.  The full-size stream (up to 32^3
+# cells, nev 2000) needs ~200 GB per request and minutes per solve.
+SERVING = dict(chains=[(6, None, 40, 48), (8, None, 60, 80), (6, (0.2, -0.1, 0.3), 30, 48),
+                       (8, (-0.3, 0.25, 0.1), 50, 64)], per_chain=16, slots=2, load=0.8, degree=25, tol=1e-8,
+               seed_arrivals=8)
+
+
+def serving_desc(prec):
+    return ("serving stream: %d requests, Poisson arrivals at %.1f x the warm single-stream solve rate, 4 chains "
+            "of 1%%-drifting FE operators (real 6^3 / 8^3 Q4 cells, complex k-point 6^3 / 8^3; nev 40 / 60 / 30 / "
+            "50), warm starts kept on the device, %d server slots, degree 25, %s filter"
+            % (SERVING["per_chain"] * len(SERVING["chains"]), SERVING["load"], SERVING["slots"], prec))
+
+
+def serving_run(args):
+    """Serving stream through rchfsi_server_create / rchfsi_submit / rchfsi_poll."""
+    from paper_2503_22652_gb300 import Server
+    prec = args.precision
+    chains = []
+    for ci, (n, kp, nev, blk) in enumerate(SERVING["chains"]):
+        kpoint = None if kp is None else 2.0 * np.pi / (n * 0.5) * np.asarray(kp)
+        probs = wl.fe_scf_chain(n, SERVING["per_chain"] + 1, seed_wells=6 + ci, seed_pert=100 + ci, kpoint=kpoint)
+        rng = np.random.default_rng(200 + ci)
+        m = probs[0]["m"]
+        X0 = rng.standard_normal((m, blk))
+        if kp is not None:
+            X0 = X0 + 1j * rng.standard_normal((m, blk))
+        chains.append(dict(probs=probs, nev=nev, block=blk, X0=X0, field="real" if kp is None else "complex"))
+    srv = Server(slots=SERVING["slots"])
+
+    def submit(ci, k, key):
+        c = chains[ci]
+        p = c["probs"][k]
+        fe = dict(cell_dofs=p["cell_dofs"], A_cells=p["A_cells"], B_cells=p["B_cell"], Dinv=p["Dinv"])
+        return srv.submit(p["m"], c["nev"], c["block"], X0=c["X0"], warm_key=key, fe=fe, field=c["field"],
+                          precision=prec, degree=SERVING["degree"], max_iter=300, tol=SERVING["tol"])
+
+    def wait(t):
+        while True:
+            r = srv.poll(t)
+            if r is not None:
+                return r
+            time.sleep(0.001)
+
+    # calibration (own warm keys): a cold then a warm solve per chain, one at a time
+    warm_ms = []
+    for ci in range(len(chains)):
+        wait(submit(ci, 0, 1000 + ci))
+        warm_ms.append(wait(submit(ci, 1, 1000 + ci))["latency_ms"])
+    S = float(np.mean(warm_ms)) / 1e3
+    rate = SERVING["load"] / S
+    # the stream: request k of every chain (k = 1..per_chain, operator k), in a seeded random order
+    order = [(ci, k) for k in range(1, SERVING["per_chain"] + 1) for ci in range(len(chains))]
+    rng = np.random.default_rng(SERVING["seed_arrivals"])
+    gaps = rng.exponential(1.0 / rate, len(order))
+    t_arr = np.cumsum(gaps) - gaps[0]
+    pending, results = {}, []
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(order) or pending:
+        now = time.perf_counter() - t0
+        while i < len(order) and t_arr[i] <= now:
+            ci, k = order[i]
+            pending[submit(ci, k, 1 + ci)] = (ci, k, now)
+            i += 1
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                ci, k, ta = pending.pop(t)
+                r["done_s"] = time.perf_counter() - t0
+                r["chain"], r["step"] = ci, k
+                results.append(r)
+        time.sleep(0.0005)
+    t_end = max(r["done_s"] for r in results)
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in results])
+    its = {ci: [r["iterations"] for r in sorted(results, key=lambda x: x["step"]) if r["chain"] == ci]
+           for ci in range(len(chains))}
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "mean_ms": round(float(lat.mean()), 2), "queue_ms_p50": round(float(np.median([r["queue_ms"] for r in results])), 2),
+            "solves_per_s": round(len(results) / t_end, 3), "requests": len(results),
+            "arrival_rate_per_s": round(rate, 3), "warm_service_ms": [round(v, 1) for v in warm_ms],
+            "statuses_ok": int(sum(r["status"] == 0 for r in results)),
+            "statuses": {str(k): int(v) for k, v in zip(*np.unique([r["status"] for r in results], return_counts=True))},
+            "failed": [(r["chain"], r["step"], r["status"], r["error"][:100]) for r in results if r["status"] != 0],
+            "max_rel_residual": float(max(r["max_rel_residual"] for r in results)),
+            "iterations_first_vs_rest": {str(ci): [v[0], round(float(np.mean(v[1:])), 1)] for ci, v in its.items()},
+            "precision": prec, "workload": serving_desc(prec)}
+
+
+def run_serving(args, rank, world, local_rank):
+    import torch
+    import paper_2503_22652_gb300.build as B
+    torch.cuda.set_device(local_rank)
+    B.build()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    r = serving_run(args)
+    clocks = clk.stop()
+    if rank != 0:
+        return None
+    return {"metric": "serving latency p50 (Poisson arrivals, warm-started outer-loop chains)", "value": r["p50_ms"],
+            "unit": "ms", "n_gpus": world, "steps": r["requests"], "warmup": 8, "ms_per_step": r["mean_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "%s+f64" % r["precision"],
+            "data": "synthetic", "config": {"workload": r["workload"], "parallelism": "single GPU"},
+            "roofline": None, "gpu_launches": None, "clocks": clocks, "e2e": None, "cpu_baseline": None,
+            "serving": {k: v for k, v in r.items() if k != "workload"}}
 
 
 def make_problem(kind):
@@ -291,7 +403,7 @@ def oracle_sample(prob, iters=2):
 def run_reference(args, rank):
     if rank != 0:
         return None
-    if args.workload == "kpoints":
+    if args.workload in ("kpoints", "serving"):
         return {"impl": "reference", "unavailable": "the oracle arm times the dense and FE workloads only"}
     prob = make_problem(args.workload)
     iters_assumed = 10 if args.workload == "dense" else 8
@@ -600,6 +712,8 @@ def main():
         out = run_reference(args, rank)
     elif args.workload == "kpoints":
         out = run_kpoints(args, rank, world, local_rank)
+    elif args.workload == "serving":
+        out = run_serving(args, rank, world, local_rank)
     else:
         out = run_gpu(args, rank, world, local_rank)
     if out is not None:

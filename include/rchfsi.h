@@ -269,6 +269,7 @@ typedef struct rchfsi_result {
   double queue_ms;    /* submit -> admission */
   double* evals;      /* caller buffer of block doubles to receive the Ritz values (may be NULL) */
   double* X;          /* caller buffer of m x block doubles for the Ritz vectors (may be NULL) */
+  char error[160];    /* text of the error when status != RCHFSI_OK (empty otherwise) */
 } rchfsi_result;
 
 /* Create / destroy a server: up to `slots` requests run concurrently, each on its own stream,

@@ -354,7 +354,8 @@ class Server:
             raise RChFSIError(rc, "poll")
         del self._pending[ticket]
         out = {"status": res.status, "iterations": res.iterations, "max_rel_residual": res.max_rel_residual,
-               "latency_ms": res.latency_ms, "queue_ms": res.queue_ms, "evals": ev}
+               "latency_ms": res.latency_ms, "queue_ms": res.queue_ms, "evals": ev,
+               "error": res.error.decode(errors="replace")}
         if X is not None:
             out["X"] = X
         return out

@@ -68,7 +68,7 @@ class rchfsi_request(C.Structure):
 class rchfsi_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("max_rel_residual", C.c_double),
                 ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("evals", C.c_void_p),
-                ("X", C.c_void_p)]
+                ("X", C.c_void_p), ("error", C.c_char * 160)]
 
 
 # name -> (restype, argtypes); the exported symbols of include/rchfsi.h

@@ -44,6 +44,7 @@ struct Job {
   int iterations = 0;
   double max_rel = 0.0;
   std::vector<double> evals, X;
+  std::string error;  // text of the failure (empty on success)
 };
 
 struct Warm {
@@ -157,6 +158,11 @@ void run_job(Server& S, Job& j) {
         }
       }
     }
+  }
+  if (rc != RCHFSI_OK) {
+    char buf[160] = {0};
+    rchfsi_last_error(h, buf, sizeof(buf));
+    j.error = buf;
   }
   rchfsi_destroy(h);
   j.status = rc;
@@ -314,6 +320,8 @@ int rchfsi_poll(rchfsi_ctx* h, uint64_t ticket, rchfsi_result* out) {
   out->max_rel_residual = job->max_rel;
   out->latency_ms = std::chrono::duration<double, std::milli>(job->t_done - job->t_submit).count();
   out->queue_ms = std::chrono::duration<double, std::milli>(job->t_admit - job->t_submit).count();
+  std::memset(out->error, 0, sizeof(out->error));
+  std::strncpy(out->error, job->error.c_str(), sizeof(out->error) - 1);
   auto put = [](double* dst, const std::vector<double>& v) {
     if (!dst || v.empty()) return;
     cudaPointerAttributes a{};

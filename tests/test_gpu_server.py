@@ -102,3 +102,25 @@ def test_budget_admission_and_errors():
     with pytest.raises(KeyError):
         srv.poll(123456)
     srv.close()
+
+
+def test_concurrent_fe_requests_of_different_widths():
+    """FE requests whose tensor-core launches use different tile widths (shared-memory plans) run
+    concurrently in several slots: every one succeeds and equals its solve alone."""
+    probs = [(wl.fe_problem(3), 6, 10, "tf32"), (wl.fe_problem(3, seed_wells=9), 20, 48, "bf16"),
+             (wl.fe_problem(2), 8, 16, "tf32"), (wl.fe_problem(3, seed_wells=10), 30, 96, "tf32")]
+    srv = Server(slots=4)
+    tickets = []
+    for p, nev, blk, prec in probs:
+        fe = dict(cell_dofs=p["cell_dofs"], A_cells=p["A_cells"], B_cells=p["B_cell"], Dinv=p["Dinv"])
+        tickets.append(srv.submit(p["m"], nev, blk, X0=wl.gaussian_block(p["m"], blk, seed=blk), fe=fe,
+                                  precision=prec, degree=20, max_iter=150))
+    res = _wait(srv, tickets)
+    srv.close()
+    for t, (p, nev, blk, prec) in zip(tickets, probs):
+        r = res[t]
+        assert r["status"] == 0, r["error"]
+        s = Solver(p["m"], nev=nev, block=blk, degree=20, precision=prec, max_iter=150)
+        s.set_fe(p["cell_dofs"], p["A_cells"], p["B_cell"], p["Dinv"])
+        _, ev, _, st = s.solve(wl.gaussian_block(p["m"], blk, seed=blk))
+        np.testing.assert_allclose(r["evals"][:nev], ev[:nev], rtol=0, atol=1e-9 * np.abs(ev[:nev]).max())

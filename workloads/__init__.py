@@ -9,9 +9,9 @@ so the oracle and the GPU path receive identical bytes.
 from .dense import (orthogonal, config1_spectrum, dense_from_spectrum, dense_config1,
                     dense_config2, toy_standard, toy_generalized, gaussian_block)
 from .fe import (gll_1d, fe_mesh, fe_problem, fe_1d_matrices, fe_config3, fe_kpoint_problem,
-                 fe_config4_list)
+                 fe_config4_list, fe_scf_chain)
 
 __all__ = ["orthogonal", "config1_spectrum", "dense_from_spectrum", "dense_config1",
            "dense_config2", "toy_standard", "toy_generalized", "gaussian_block",
            "gll_1d", "fe_mesh", "fe_problem", "fe_1d_matrices", "fe_config3",
-           "fe_kpoint_problem", "fe_config4_list"]
+           "fe_kpoint_problem", "fe_config4_list", "fe_scf_chain"]

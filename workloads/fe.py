@@ -166,6 +166,20 @@ def fe_kpoint_problem(n, kappa, **kw):
     return fe_problem(n, kpoint=2.0 * np.pi / box * np.asarray(kappa), **kw)
 
 
+def fe_scf_chain(n, steps, seed_wells=6, seed_pert=100, rel=0.01, kpoint=None):
+    """A sequence of FE problems whose well depths drift by a seeded relative perturbation `rel`
+    per step (each step perturbs the previous one), as in the successive operators of an outer
+    self-consistency loop.  kpoint as in fe_problem."""
+    box = n * 0.5
+    d, w, c = _wells(8, box, seed_wells)
+    r = np.random.default_rng(seed_pert)
+    out = []
+    for _ in range(steps):
+        out.append(fe_problem(n, wells=(d.copy(), w, c), kpoint=kpoint))
+        d = d * (1.0 + rel * r.standard_normal(d.shape))
+    return out
+
+
 def fe_config4_list(n_problems=16, seed=7, nmin=8, nmax=20, nev_range=(100, 800)):
     """Specs of the batched k-point workload: cells per dimension, nev, block N and the
     reduced Bloch vector kappa in [-0.5, 0.5)^3 for each problem (matrices are built
