@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "fe", "kpoints", "serving"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "fe", "kpoints", "serving", "psweep"])
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison runs")
     ap.add_argument("--rr", default="emulated", choices=["fp64", "emulated"],
@@ -260,6 +260,50 @@ def run_serving(args, rank, world, local_rank):
             "serving": {k: v for k, v in r.items() if k != "workload"}}
 
 
+def psweep_run(args, torch, dev):
+    """Degree sweep on the dense benchmark problem: time to 1e-8 and iterations per degree and
+    precision (where the reduced-precision filter stops paying for higher degrees)."""
+    from paper_2503_22652_gb300 import Solver
+    prob = make_problem("dense")
+    c = prob["dense"]
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    dA, dB, dD, X0 = T(c["A"]), T(c["B"]), T(c["Dinv"]), T(prob["X0"])
+    out = []
+    for prec in ("tf32", "bf16", "fp32"):
+        for p in (10, 20, 30, 40, 60, 80, 120):
+            s = Solver(prob["m"], nev=prob["nev"], block=prob["block"], degree=p, precision=prec, max_iter=300,
+                       tol=prob["tol"], rr_mode=args.rr, eig_mode=args.eig)
+            s.set_dense(dA, B=dB, Dinv=dD)
+            s.solve(X0.clone(), allow_not_converged=True)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, ev, res, st = s.solve(X0.clone(), allow_not_converged=True)
+            torch.cuda.synchronize()
+            out.append({"precision": prec, "degree": p, "ms": round((time.perf_counter() - t0) * 1e3, 1),
+                        "iterations": st["iterations"], "status": st["status"],
+                        "max_rel_residual": st["max_rel_residual"], "t_filter_ms": round(st["t_filter_ms"], 1)})
+            s.close()
+    return out
+
+
+def run_psweep(args, rank, world, local_rank):
+    import torch
+    import paper_2503_22652_gb300.build as B
+    torch.cuda.set_device(local_rank)
+    B.build()
+    r = psweep_run(args, torch, torch.device("cuda", local_rank))
+    if rank != 0:
+        return None
+    best = min((x for x in r if x["status"] == 0), key=lambda x: x["ms"])
+    return {"metric": "R-ChFSI time-to-1e-8 relative residual, best degree", "value": best["ms"], "unit": "ms",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": best["ms"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "%s+f64" % best["precision"], "data": "synthetic",
+            "config": {"workload": workload_desc("dense", "swept") + "; degree swept 10..120",
+                       "parallelism": "single GPU"},
+            "roofline": None, "gpu_launches": None, "clocks": None, "e2e": None, "cpu_baseline": None,
+            "best": best, "sweep": r}
+
+
 def make_problem(kind):
     if kind == "dense":
         c = wl.dense_config2(m=DENSE["m"])
@@ -403,7 +447,7 @@ def oracle_sample(prob, iters=2):
 def run_reference(args, rank):
     if rank != 0:
         return None
-    if args.workload in ("kpoints", "serving"):
+    if args.workload in ("kpoints", "serving", "psweep"):
         return {"impl": "reference", "unavailable": "the oracle arm times the dense and FE workloads only"}
     prob = make_problem(args.workload)
     iters_assumed = 10 if args.workload == "dense" else 8
@@ -714,6 +758,8 @@ def main():
         out = run_kpoints(args, rank, world, local_rank)
     elif args.workload == "serving":
         out = run_serving(args, rank, world, local_rank)
+    elif args.workload == "psweep":
+        out = run_psweep(args, rank, world, local_rank)
     else:
         out = run_gpu(args, rank, world, local_rank)
     if out is not None:
