@@ -28,10 +28,18 @@ struct FeOp {
   bool cplx = false;
   int64_t mc = 0;
   std::unique_ptr<FeOp> imag;
+  // FP64-accurate tensor-core products (fe_oz.cu): BF16 slice images of the cell matrices (made on
+  // first use) and per-product scratch (column exponents, slice planes of the input block)
+  mutable DevBuf<uint8_t> ozA, ozB;
+  mutable DevBuf<int> ozAe, ozBe, ozcexp;
+  mutable DevBuf<__nv_bfloat16> ozplanes;
 };
 
 // Y (row-major m x n) = Op X, Op = A or B, FP64.  Y is overwritten.
 void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n);
+// Same product, FP64-accurate, from exact BF16 slices on the tensor cores (fe_oz.cu).
+void fe_apply_f64_rows_tc(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n,
+                          int num_sms);
 
 // Filter product for FE operators on row-major m x n blocks, accumulated into Rx (the
 // product-free recurrence terms are applied to Rx beforehand):

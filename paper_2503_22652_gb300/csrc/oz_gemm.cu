@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "oz_gemm.cuh"
+#include "oz_digits.cuh"
 #include "prof.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,40 +35,6 @@ constexpr uint32_t kBBytes = S * BN * 128;   // 28 KB: all B slices of one chunk
 constexpr uint32_t kTmemCols = 512;          // 2 buffers x 7 levels x 32 columns = 448
 
 // ---------------------------------------------------------------- slicing
-// FP64 arithmetic is scarce on this GPU, so the slicing works on the bits: the binary exponent E
-// with |x| in [2^(E-1), 2^E) (E = -100000 for 0), and the digits of x 2^(56 - e) in base 256 by
-// integer shifts.
-__device__ __forceinline__ int exp_of(double x) {
-  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
-  if (b == 0) return -100000;
-  const int eb = (int)(b >> 52);
-  if (eb != 0) return eb - 1022;
-  // subnormal: 2^-1074 times the 52-bit fraction
-  return -1074 + (64 - __clzll(b));
-}
-
-// round(x 2^(56 - e)) as a signed 64-bit integer, for |x| < 2^e (so |result| <= 2^56).
-__device__ __forceinline__ long long fixed56(double x, int e) {
-  const long long bits = __double_as_longlong(x);
-  const long long b = bits & 0x7fffffffffffffffLL;
-  if (b == 0) return 0;
-  const int eb = (int)(b >> 52);
-  long long mant = b & 0x000fffffffffffffLL;
-  int ex;  // x = mant 2^ex
-  if (eb != 0) {
-    mant |= 0x0010000000000000LL;
-    ex = eb - 1075;
-  } else {
-    ex = -1074;
-  }
-  const int sh = ex + 56 - e;  // <= 4 since |x| < 2^e
-  long long f;
-  if (sh >= 0) f = mant << sh;
-  else if (sh > -63) f = (mant + (1LL << (-sh - 1))) >> (-sh);
-  else f = 0;
-  return bits < 0 ? -f : f;
-}
-
 // Row exponents, K-contiguous rows: one warp per row.
 __global__ void rowexp_kcontig(int64_t R, int64_t K, const double* __restrict__ X, int64_t rs, int* ex) {
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;

@@ -102,3 +102,31 @@ def test_fe_solve_small_mesh(precision):
     X, ev, res, st = s.solve(X0)
     assert st["max_rel_residual"] <= 1e-8
     np.testing.assert_allclose(ev[:7], ref, atol=1e-9 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("N", [1, 7, 64, 100, 131])
+def test_fe_fp64_products_tensor_core_parity(fe3, N):
+    """The FP64-accurate FE products from BF16 slices (rr_mode "emulated", several 64-wide column
+    tiles, widths that are not a multiple of 8) equal the assembled-matrix products to FP64
+    accuracy, like the DFMA path."""
+    p, A, B = fe3
+    X, L, W = _inputs(p, A, B, N, seed=N)
+    for mode in ("emulated", "fp64"):
+        s = _solver(p, N, rr_mode=mode)
+        Wg, _ = s.residual(X, L)
+        assert relfro(Wg, W) <= 1e-13, mode
+
+
+def test_fe_fp64_products_tensor_core_complex():
+    q = wl.fe_kpoint_problem(3, (0.3, -0.2, 0.1))
+    A = ofe.assemble(q["cell_dofs"], q["A_cells"], q["m"])
+    B = ofe.assemble(q["cell_dofs"], q["B_cell"], q["m"])
+    rng = np.random.default_rng(8)
+    N = 70
+    X = rng.standard_normal((q["m"], N)) + 1j * rng.standard_normal((q["m"], N))
+    L = np.sort(rng.uniform(-20.0, 30.0, N))
+    W = A @ X - (B @ X) * L[None, :]
+    s = Solver(q["m"], nev=10, block=N, field="complex", rr_mode="emulated")
+    s.set_fe(q["cell_dofs"], q["A_cells"], q["B_cell"], q["Dinv"])
+    Wg, _ = s.residual(X, L)
+    assert relfro(Wg, W) <= 1e-13
