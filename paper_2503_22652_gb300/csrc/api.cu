@@ -825,15 +825,26 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
       c.rr_paired = true;
     }
   }
+  // FE operators: A X and B X are applied directly (a cell product costs 2 n_c^2 C per column,
+  // below the 2 m N of rotating A Y and B Y, and gives the residual of X itself); dense operators
+  // rotate A Y and B Y (2 m N per column against 2 m^2)
+  bool direct = false;
+  if (c.op_kind == RCHFSI_OP_FE_CELL) {
+    // per column: a (complex: four) cell product(s), 2 n_c^2 C each, against the rotation's 2 m N
+    const double cell = (double)c.fe->nc * c.fe->nc * (double)c.fe->n_cells * (c.fe->cplx ? 4.0 : 1.0);
+    direct = cell < (double)m * N;
+  }
   if (emu) {
     // E^T as ncol logical rows (row j = column j of E, contiguous); blocks as m logical rows (dofs)
     oz_slice(c.s, ncol, N, Erot, N, 1, w.ozE);
     oz_slice(c.s, m, N, Y, 1, m, w.ozL);
     oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, X, m, w.ozws, eflag);
-    oz_slice(c.s, m, N, AY, 1, m, w.ozL);
-    oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, AX, m, w.ozws, eflag);
-    oz_slice(c.s, m, N, BY, 1, m, w.ozL);
-    oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, BX, m, w.ozws, eflag);
+    if (!direct) {
+      oz_slice(c.s, m, N, AY, 1, m, w.ozL);
+      oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, AX, m, w.ozws, eflag);
+      oz_slice(c.s, m, N, BY, 1, m, w.ozL);
+      oz_gemm(c.s, c.num_sms, w.ozL, w.ozE, BX, m, w.ozws, eflag);
+    }
     int flag = 0;
     RC_CUDA(cudaMemcpyAsync(&flag, eflag, sizeof(int), cudaMemcpyDeviceToHost, c.s));
     RC_CUDA(cudaStreamSynchronize(c.s));
@@ -843,11 +854,20 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
     }
   } else {
     gemm_f64(c.s, m, ncol, N, Y, m, false, Erot, N, true, epi_store(X, m));
-    gemm_f64(c.s, m, ncol, N, AY, m, false, Erot, N, true, epi_store(AX, m));
-    gemm_f64(c.s, m, ncol, N, BY, m, false, Erot, N, true, epi_store(BX, m));
+    if (!direct) {
+      gemm_f64(c.s, m, ncol, N, AY, m, false, Erot, N, true, epi_store(AX, m));
+      gemm_f64(c.s, m, ncol, N, BY, m, false, Erot, N, true, epi_store(BX, m));
+    }
   }
-  if (c.rr_paired) {
-    jcomplete(X);
+  if (c.rr_paired) jcomplete(X);
+  if (direct) {
+    apply_A_f64(c, X, AX, ncol);
+    apply_B_f64(c, X, BX, ncol);
+    if (c.rr_paired) {
+      jcomplete(AX);
+      jcomplete(BX);
+    }
+  } else if (c.rr_paired) {
     jcomplete(AX);
     jcomplete(BX);
   }
