@@ -5,15 +5,16 @@
 // Per (cell, column tile) work item: D (128 x BN, FP32 in TMEM) = A_c (128 x 128, cell matrix padded
 // from n_c <= 128) x X_c (128 x BN, the cell's rows of the block).  A persistent CTA per SM walks its
 // cells; for each cell it streams the column tiles.  Warp roles:
-//   warps 0-3  gather: thread k reads row dofs(c)[k] of R_Y (16-byte loads), scales by D^-1, rounds
-//              to the operand type and writes it transposed into the K-major 128-byte-swizzled
-//              shared-memory image of X_c (two stages), then fence.proxy.async + mbarrier arrive;
-//   warp 4     MMA issuer (one lane): tcgen05.mma kind::tf32 (K = 8) or kind::f16 (BF16, K = 16)
+//   warps 0-7  gather: thread (k, h) reads half of row dofs(c)[k] of the tile of R_Y (eight 16-byte
+//              loads in flight), scales by D^-1, rounds to the operand type and writes it transposed
+//              into the K-major 128-byte-swizzled shared-memory image of X_c (two stages), then
+//              fence.proxy.async + mbarrier arrive;
+//   warp 8     MMA issuer (one lane): tcgen05.mma kind::tf32 (K = 8) or kind::f16 (BF16, K = 16)
 //              into one of two TMEM accumulators, tcgen05.commit to release stages / buffers;
-//   warps 5-8  epilogue: tcgen05.ld of the accumulator rows (thread = cell-local dof), scaling, and
+//   warps 9-12 epilogue: tcgen05.ld of the accumulator rows (thread = cell-local dof), scaling, and
 //              vectorised float4 atomic scatter-add into R_X (dofs shared by neighbouring cells get
 //              one add per cell);
-//   warp 9     cell-matrix loader: one cp.async.bulk of the pre-swizzled cell-matrix image (two
+//   warp 13    cell-matrix loader: one cp.async.bulk of the pre-swizzled cell-matrix image (two
 //              buffers, so the next cell's matrix streams in while the current one is in use).
 // The cell-matrix images are built once per operator and precision by a packing kernel.  Every
 // mbarrier wait is bounded; on a timeout the kernel raises the error flag and unwinds.
@@ -34,7 +35,7 @@ namespace rchfsi {
 namespace {
 
 constexpr int kNCP = 128;         // padded cell size (MMA M and K)
-constexpr int kThreads = 320;     // 10 warps
+constexpr int kThreads = 448;     // 14 warps
 constexpr int kRowBytes = 128;
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&afull[i], 1);
       tc::mbar_init(&aempty[i], 1);
-      tc::mbar_init(&bfull[i], 128);
+      tc::mbar_init(&bfull[i], 256);
       tc::mbar_init(&bempty[i], 1);
       tc::mbar_init(&accfull[i], 1);
       tc::mbar_init(&accempty[i], 128);
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
     tc::fence_barrier_init();
     abort_flag = 0;
   }
-  if (warp == 4) {
+  if (warp == 8) {
     tc::tmem_alloc(&tmem_slot, p.tmem_cols);
     tc::tmem_relinquish();
     tc::tc_fence_before();
@@ -154,15 +155,16 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
   };
   const int64_t G = gridDim.x;
 
-  if (warp < 4) {
-    // ---------------- gather: thread k owns cell-local dof k
-    const int k = threadIdx.x;
+  if (warp < 8) {
+    // ---------------- gather: thread (k, h) owns cell-local dof k, columns h*BN/2 .. of the tile;
+    // eight 16-byte loads are issued before any is used, to keep enough bytes in flight
+    const int k = threadIdx.x & 127, h = threadIdx.x >> 7;
     int64_t j = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
       const FePart& P = p.part[part_of(p, g)];
       const int64_t cell = g - P.cell_off;
-      const int BN = P.BN;
+      const int BN = P.BN, half = BN / 2;
       int gi = -1;
       float sc = 0.f;
       if (k < P.nc) {
@@ -178,33 +180,42 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
           break;
         }
         uint8_t* img = sB[bs];
-        const int n0 = t * BN;
-        for (int nn = 0; nn < BN; nn += 4) {
-          float v[4] = {0.f, 0.f, 0.f, 0.f};
-          const int col = n0 + nn;
-          if (row) {
-            if (P.vec && col + 3 < P.n) {
-              const float4 q = __ldg(reinterpret_cast<const float4*>(row + col));
-              v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else {
+        const int c0 = t * BN + h * half;  // first column of this thread
+        for (int nn = 0; nn < half; nn += 32) {
+          float4 q[8];
 #pragma unroll
-              for (int u = 0; u < 4; ++u)
-                if (col + u < P.n) v[u] = __ldg(row + col + u);
+          for (int u = 0; u < 8; ++u) {
+            const int cc = nn + 4 * u, col = c0 + cc;
+            q[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row && cc < half) {
+              if (P.vec && col + 3 < P.n) {
+                q[u] = __ldg(reinterpret_cast<const float4*>(row + col));
+              } else {
+                float* f = reinterpret_cast<float*>(&q[u]);
+                for (int w = 0; w < 4; ++w)
+                  if (col + w < P.n) f[w] = __ldg(row + col + w);
+              }
             }
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float x = v[u] * sc;
-            uint8_t* dst = img + sw_off<ES>(nn + u, k, BN);
-            if (BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(x);
-            else *reinterpret_cast<float*>(dst) = tf32_rna(x);
+          for (int u = 0; u < 8; ++u) {
+            const int cc = nn + 4 * u;
+            if (cc >= half) break;
+            const float* f = reinterpret_cast<const float*>(&q[u]);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              const float x = f[w] * sc;
+              uint8_t* dst = img + sw_off<ES>(h * half + cc + w, k, BN);
+              if (BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(x);
+              else *reinterpret_cast<float*>(dst) = tf32_rna(x);
+            }
           }
         }
         fence_proxy_async();
         tc::mbar_arrive(&bfull[bs]);
       }
     }
-  } else if (warp == 4) {
+  } else if (warp == 8) {
     // ---------------- MMA issuer
     if (lane == 0) {
       int64_t j = 0, cl = 0;
@@ -246,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
         }
       }
     }
-  } else if (warp < 9) {
+  } else if (warp < 13) {
     // ---------------- epilogue: TMEM -> scatter-add
     const int q = warp & 3;
     const int i = q * 32 + lane;  // cell-local dof of this thread's accumulator row
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
       }
     }
   } else {
-    // ---------------- cell-matrix loader (warp 9, one lane)
+    // ---------------- cell-matrix loader (warp 13, one lane)
     if (lane == 0) {
       int64_t issued = 0, cl = 0;
       for (int64_t g = blockIdx.x; g < p.total_cells; g += G, ++cl) {
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
     }
   }
   __syncthreads();
-  if (warp == 4) {
+  if (warp == 8) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, p.tmem_cols);
   }
