@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(EIG_THREADS) tridiag_kernel(int n, double* M, 
     for (int c = c0 + warp * P; c < n; c += nw * P) {
       double* mc = M + (int64_t)c * n + k + 1;
       const double wc = w[c - k - 1], vc = v[c - k - 1];
-      for (int i = lane; i < rr; i += 32) mc[i] -= v[i] * wc + w[i] * vc;
+      for (int i = lane; i < rr; i += 32) mc[i] = fma(-w[i], vc, fma(-v[i], wc, mc[i]));
     }
     all_sync<CLUSTER>();
   }
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_smem_kernel(int n, const 
         const int c = r + q * P;
         double* mc = cols + (size_t)q * n + k + 1;
         const double wc = w[c - k - 1], vc = v[c - k - 1];
-        for (int i = lane; i < rr; i += 32) mc[i] -= v[i] * wc + w[i] * vc;
+        for (int i = lane; i < rr; i += 32) mc[i] = fma(-w[i], vc, fma(-v[i], wc, mc[i]));
       }
       __syncthreads();
     }
@@ -408,41 +408,59 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_smem_kernel(int n, const 
 // way; an exact zero is replaced by a tiny value of the sign opposite to its predecessor.
 __device__ __forceinline__ bool neg_bits(double v) { return __double_as_longlong(v) < 0; }
 
-__device__ int sturm_count(int n, const double* ds, const double* e2s, double xs) {
-  double pm = 1.0;
-  double p = ds[0] - xs;
-  if ((__double_as_longlong(p) << 1) == 0) p = -DBL_MIN;
-  int cnt = neg_bits(p);
+template <int K>
+__device__ void sturm_count_k(int n, const double* ds, const double* e2s, const double* xs, int* cnt) {
+  // K independent sequences interleaved, so their dependent FMAs overlap
+  double pm[K], p[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    pm[c] = 1.0;
+    p[c] = ds[0] - xs[c];
+    if ((__double_as_longlong(p[c]) << 1) == 0) p[c] = -DBL_MIN;
+    cnt[c] = neg_bits(p[c]);
+  }
   int i = 1;
   for (; i + 8 <= n; i += 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const double a = ds[i + u] - xs;
-      double pn = fma(a, p, -e2s[i + u] * pm);
-      if ((__double_as_longlong(pn) << 1) == 0) pn = neg_bits(p) ? DBL_MIN : -DBL_MIN;
-      cnt += neg_bits(pn) != neg_bits(p);
-      pm = p;
-      p = pn;
+      const double d = ds[i + u], e2 = e2s[i + u];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        double pn = fma(d - xs[c], p[c], -e2 * pm[c]);
+        if ((__double_as_longlong(pn) << 1) == 0) pn = neg_bits(p[c]) ? DBL_MIN : -DBL_MIN;
+        cnt[c] += neg_bits(pn) != neg_bits(p[c]);
+        pm[c] = p[c];
+        p[c] = pn;
+      }
     }
-    const long long bp = __double_as_longlong(p) & 0x7fffffffffffffffLL;
-    const long long bq = __double_as_longlong(pm) & 0x7fffffffffffffffLL;
-    const long long ex = ((bp > bq ? bp : bq) >> 52) - 1023;
-    const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
-    p *= sc;
-    pm *= sc;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const long long bp = __double_as_longlong(p[c]) & 0x7fffffffffffffffLL;
+      const long long bq = __double_as_longlong(pm[c]) & 0x7fffffffffffffffLL;
+      const long long ex = ((bp > bq ? bp : bq) >> 52) - 1023;
+      const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+      p[c] *= sc;
+      pm[c] *= sc;
+    }
   }
   for (; i < n; ++i) {
-    const double a = ds[i] - xs;
-    double pn = fma(a, p, -e2s[i] * pm);
-    if ((__double_as_longlong(pn) << 1) == 0) pn = neg_bits(p) ? DBL_MIN : -DBL_MIN;
-    cnt += neg_bits(pn) != neg_bits(p);
-    pm = p;
-    p = pn;
+    const double d = ds[i], e2 = e2s[i];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double pn = fma(d - xs[c], p[c], -e2 * pm[c]);
+      if ((__double_as_longlong(pn) << 1) == 0) pn = neg_bits(p[c]) ? DBL_MIN : -DBL_MIN;
+      cnt[c] += neg_bits(pn) != neg_bits(p[c]);
+      pm[c] = p[c];
+      p[c] = pn;
+    }
   }
-  return cnt;
 }
 
-// Eigenvalue j (ascending) of T = tridiag(e, d, e): one warp (one CTA), 32 trial points per step.
+// Sturm sequences per lane.  One: on this GPU a warp-wide FP64 instruction occupies the SM's FP64
+// pipe for ~12 clocks, so more sequences per lane trade latency for pipe time at a loss (measured).
+constexpr int kChains = 1;
+
+// Eigenvalue j (ascending) of T = tridiag(e, d, e): one warp (one CTA), 32 kChains trial points per step.
 __global__ void __launch_bounds__(32) bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                                                     double* lam, double* tnorm_out) {
   extern __shared__ double sm[];
@@ -472,20 +490,32 @@ __global__ void __launch_bounds__(32) bisect_kernel(int n, const double* __restr
   const double tiny = DBL_MIN * 4.0;
   lo -= 2.0 * DBL_EPSILON * tnorm + tiny;
   hi += 2.0 * DBL_EPSILON * tnorm + tiny;
+  constexpr int NP = 32 * kChains;  // trial points per step; point q = c * 32 + lane
   for (int it = 0; it < 64; ++it) {
     // relative accuracy, but no finer than the eps ||T|| that the Sturm counts resolve
     if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 0.5 * DBL_EPSILON * tnorm + tiny) break;
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm_count(n, ds, e2s, x * inv_tn);
-    const unsigned ge = __ballot_sync(0xffffffffu, cnt >= j + 1);
-    if (ge == 0u) {
-      lo = __shfl_sync(0xffffffffu, x, 31);
+    const double w = (hi - lo) / (double)(NP + 1);
+    double x[kChains], xs[kChains];
+    int cnt[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      x[c] = lo + w * (double)(c * 32 + lane + 1);
+      xs[c] = x[c] * inv_tn;
+    }
+    sturm_count_k<kChains>(n, ds, e2s, xs, cnt);
+    // counts grow with x, so the first point with count > j bounds the eigenvalue from above
+    int q = -1;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      const unsigned ge = __ballot_sync(0xffffffffu, cnt[c] >= j + 1);
+      if (q < 0 && ge != 0u) q = c * 32 + __ffs(ge) - 1;
+    }
+    if (q < 0) {
+      lo = lo + w * (double)NP;
     } else {
-      const int l = __ffs(ge) - 1;
-      const double xl = __shfl_sync(0xffffffffu, x, l);
-      const double xm = __shfl_sync(0xffffffffu, x, l > 0 ? l - 1 : 0);
-      hi = xl;
-      if (l > 0) lo = xm;
+      const double nlo = q > 0 ? lo + w * (double)q : lo;
+      hi = lo + w * (double)(q + 1);
+      lo = nlo;
     }
   }
   if (lane == 0) {
@@ -604,7 +634,8 @@ __global__ void __launch_bounds__(32) inviter_kernel(int n, const double* __rest
     nr = warp_sum(nr);
     for (int m = lane; m < n; m += 32) y[m] *= rsqrt(nr);
     __syncwarp();
-    for (int it = 0; it < 3; ++it) {
+    // the shift is accurate to a few ulps, so two solves already give the eigenvector to round-off
+    for (int it = 0; it < 2; ++it) {
       if (lane == 0) tri_solve(n, u0, u1, u2, mult, sw, y);
       __syncwarp();
       for (int rep = 0; rep < 2; ++rep) {
