@@ -149,9 +149,6 @@ void resid_rel_norms(cudaStream_t s, int64_t m, int64_t n, const double* W, cons
                      double* out_xnorm);
 
 // Small dense FP64 kernels (N x N, column-major).
-int cholesky_f64(cudaStream_t s, int n, double* A, int lda, int* d_info);  // lower, in place
-void trsm_lower_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
-void trsm_lower_trans_left_f64(cudaStream_t s, int n, int nrhs, const double* L, int ldl, double* B, int ldb);
 void symmetrize_f64(cudaStream_t s, int n, double* A, int lda);
 // Cholesky G = L L^T and L^-1 (small_eig.cu): A (n x n, col-major) destroyed; L, Linv lower triangular.
 int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Linv, int* d_info, int num_sms,

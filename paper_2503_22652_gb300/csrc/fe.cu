@@ -149,18 +149,14 @@ void fe_filter_product_f64(cudaStream_t s, const FeOp& op, const double* Ry, dou
   });
 }
 
-static void fe_product_f32_one(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
-                               int dmode) {
+// FP32 (FFMA) filter product of one real part.
+static void fe_product_f32_one(cudaStream_t s, FeOp& op, const float* Ry, float* Rx, int n, float a, int dmode) {
   const size_t na = (size_t)op.n_cells * op.nc * op.nc;
-  if (precision == RCHFSI_FP32) {
-    if (!op.A32.p) {
-      op.A32.ensure(na);
-      cast_f64_to_f32(s, na, op.A64.p, op.A32.p, 1.0, 0);
-    }
-    launch_cells<float, 64>(s, op, op.A32.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode, RCHFSI_KERNEL_FE_CELL);
-    return;
+  if (!op.A32.p) {
+    op.A32.ensure(na);
+    cast_f64_to_f32(s, na, op.A64.p, op.A32.p, 1.0, 0);
   }
-  fe_tc_product(s, op, precision, Ry, Rx, n, a, dmode);
+  launch_cells<float, 64>(s, op, op.A32.p, (int64_t)op.nc * op.nc, Ry, Rx, n, a, dmode, RCHFSI_KERNEL_FE_CELL);
 }
 
 void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float* Ry, float* Rx, int n, float a,
@@ -171,7 +167,7 @@ void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float*
     return;
   }
   complex_parts<float>(op, false, Ry, Rx, n, a, [&](const FeOp& o, const float* x, float* y, float al) {
-    fe_product_f32_one(s, const_cast<FeOp&>(o), precision, x, y, n, al, dmode);
+    fe_product_f32_one(s, const_cast<FeOp&>(o), x, y, n, al, dmode);
   });
 }
 
