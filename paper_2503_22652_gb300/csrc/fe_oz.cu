@@ -8,17 +8,19 @@
 // product is then 28 slice products A_c^(s) X_c^(t), s + t <= 6, each a 128 x BN x 128 tcgen05 MMA;
 // the products of one level L = s + t sum to an integer that FP32 holds exactly (levels <= 5; the
 // last level, weight 2^-48, at most one unit off), so the 7 level accumulators live in TMEM and are
-// folded once per tile.
+// folded once per tile, in float-float (a 2^-48 relative rounding per cell contribution, the order
+// of an FP64 dot product's own rounding over the 125 terms of a cell row).
 //
-// fe_oz_kernel, one persistent CTA per SM walking (cell, column tile) items, 448 threads:
+// fe_oz_kernel, one persistent CTA per SM walking (cell, column tile) items, 576 threads:
 //   warps 0-7  gather: thread (k, h) copies its dof k's row, columns h*BN/2.., of the 7 X slice
 //              planes (sliced once per product by xslice_kernel) into the K-major 128-byte-swizzled
 //              shared images X_c^(t);
 //   warp 8     MMA issuer (one lane): for each A slice s (streamed through a 2-deep ring) the
 //              products with X_c^(t), t <= 6 - s, into the TMEM accumulator of level s + t;
-//   warps 9-12 epilogue: tcgen05.ld of the 7 levels, float-float fold of levels 1..6, one FP64 add
-//              of level 0, exponent scaling by integer arithmetic, FP64 atomic scatter-add;
-//   warp 13    cell-slice loader (one lane): cp.async.bulk of the 32 KB A_c^(s) images.
+//   warps 9-16 epilogue (two per TMEM lane quarter, alternate 16 columns): tcgen05.ld of the 7
+//              levels, float-float fold, exact conversion and exponent scaling by integer
+//              arithmetic, one FP64 add, FP64 atomic scatter-add;
+//   warp 17    cell-slice loader (one lane): cp.async.bulk of the 32 KB A_c^(s) images.
 // Every mbarrier wait is bounded; on a timeout the kernel raises the error flag and unwinds.
 #include "fe.cuh"
 #include "oz_digits.cuh"
@@ -32,7 +34,7 @@ namespace {
 
 constexpr int S = 7;               // slices per operand
 constexpr int kNCP = 128;          // padded cell size (M and K)
-constexpr int kThreads = 448;      // 14 warps
+constexpr int kThreads = 576;      // 18 warps
 constexpr int kMaxBN = 64;
 constexpr uint32_t kASlice = kNCP * kNCP * 2;  // 32 KB per A slice image
 constexpr int kRowBytes = 128;
@@ -118,6 +120,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// OR of v over the 256 epilogue threads (named barrier 1); every epilogue warp must call it.
+__device__ __forceinline__ bool epi_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, 256, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
   const float s = hi + b;
   const float bb = s - hi;
@@ -141,6 +155,7 @@ __device__ __forceinline__ double f32_scaled(float x, int p) {
 __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constant__ FeOzArgs p) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t afull[2], aempty[2], xfull, xempty, accfull, accempty;
+  __shared__ int s_cexp[kMaxBN];  // column exponents of the current tile (epilogue)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -157,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
     tc::mbar_init(&xfull, 256);
     tc::mbar_init(&xempty, 1);
     tc::mbar_init(&accfull, 1);
-    tc::mbar_init(&accempty, 128);
+    tc::mbar_init(&accempty, 256);
     tc::fence_barrier_init();
     abort_flag = 0;
   }
@@ -191,27 +206,50 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
       }
       const int g = (k < p.nc) ? p.dofs[cell * p.nc + k] : -1;
       const int c0 = t * BN + h * half;
-      for (int s = 0; s < S; ++s) {
-        const __nv_bfloat16* row = (g >= 0) ? p.planes + (int64_t)s * p.plane_stride + (int64_t)g * p.n : nullptr;
-        uint8_t* img = sX + (size_t)s * x_bytes;
-        if (p.vec) {
-          // 8 columns per 16-byte load (rows start on 16-byte boundaries when n % 8 == 0)
-          for (int u = 0; u < half; u += 8) {
-            const int col = c0 + u;
-            uint4 q = make_uint4(0u, 0u, 0u, 0u);
-            if (row && col + 7 < p.n) {
-              q = __ldg(reinterpret_cast<const uint4*>(row + col));
-            } else if (row) {
-              __nv_bfloat16 tmp[8];
-              for (int w = 0; w < 8; ++w) tmp[w] = (col + w < p.n) ? row[col + w] : __float2bfloat16_rn(0.f);
-              q = *reinterpret_cast<const uint4*>(tmp);
-            }
-            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&q);
+      if (p.vec) {
+        // two planes at a time, each thread's 32 columns as four 16-byte loads per plane: eight
+        // loads in flight before any is stored (rows start on 16-byte boundaries when n % 8 == 0)
+        for (int s0 = 0; s0 < S; s0 += 2) {
+          uint4 q[2][4];
 #pragma unroll
-            for (int w = 0; w < 8; ++w)
-              *reinterpret_cast<__nv_bfloat16*>(img + sw_off2(h * half + u + w, k, BN)) = v8[w];
+          for (int d = 0; d < 2; ++d) {
+            const int s = s0 + d;
+            const __nv_bfloat16* row =
+                (g >= 0 && s < S) ? p.planes + (int64_t)s * p.plane_stride + (int64_t)g * p.n : nullptr;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int cc = 8 * u, col = c0 + cc;
+              q[d][u] = make_uint4(0u, 0u, 0u, 0u);
+              if (row && cc < half) {
+                if (col + 7 < p.n) {
+                  q[d][u] = __ldg(reinterpret_cast<const uint4*>(row + col));
+                } else {
+                  __nv_bfloat16* t8 = reinterpret_cast<__nv_bfloat16*>(&q[d][u]);
+                  for (int w = 0; w < 8; ++w) t8[w] = (col + w < p.n) ? row[col + w] : __float2bfloat16_rn(0.f);
+                }
+              }
+            }
           }
-        } else {
+#pragma unroll
+          for (int d = 0; d < 2; ++d) {
+            const int s = s0 + d;
+            if (s >= S) break;
+            uint8_t* img = sX + (size_t)s * x_bytes;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int cc = 8 * u;
+              if (cc >= half) break;
+              const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&q[d][u]);
+#pragma unroll
+              for (int w = 0; w < 8; ++w)
+                *reinterpret_cast<__nv_bfloat16*>(img + sw_off2(h * half + cc + w, k, BN)) = v8[w];
+            }
+          }
+        }
+      } else {
+        for (int s = 0; s < S; ++s) {
+          const __nv_bfloat16* row = (g >= 0) ? p.planes + (int64_t)s * p.plane_stride + (int64_t)g * p.n : nullptr;
+          uint8_t* img = sX + (size_t)s * x_bytes;
           for (int u = 0; u < half; ++u) {
             const int col = c0 + u;
             __nv_bfloat16 v = __float2bfloat16_rn(0.f);
@@ -224,58 +262,76 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
       tc::mbar_arrive(&xfull);
     }
   } else if (warp == 8) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = tc::instr_desc(1u, kNCP, BN);  // BF16 x BF16 -> FP32
-      for (int64_t j = 0; j < items; ++j) {
-        bool ok = !*vabort && tc::mbar_wait(&xfull, (uint32_t)(j & 1));
-        if (ok) ok = tc::mbar_wait(&accempty, (uint32_t)(j & 1) ^ 1u);
-        if (!ok) {
-          fail();
-          break;
-        }
-        tc::tc_fence_after();
-        for (int s = 0; s < S && ok; ++s) {
-          const int64_t a = j * S + s;
-          const int q = (int)(a & 1);
-          if (*vabort || !tc::mbar_wait(&afull[q], (uint32_t)((a >> 1) & 1))) {
-            ok = false;
-            break;
-          }
-          tc::tc_fence_after();
-          const uint32_t a_base = tc::smem_u32(sA + (size_t)q * kASlice);
-          for (int t = 0; t + s < S; ++t) {
-            const uint32_t d = tmem + (uint32_t)((s + t) * BN);
-            const uint32_t x_base = tc::smem_u32(sX + (size_t)t * x_bytes);
+    // ---------------- MMA issuer: the whole warp walks the fully unrolled (s, t, k) sequence with
+    // warp-uniform values, one elected lane issues (a runtime loop issued from one divergent lane
+    // ran the tensor pipe at about two thirds of this rate)
+    const bool leader = tc::elect_one();
+    const uint32_t idesc = tc::instr_desc(1u, kNCP, BN);  // BF16 x BF16 -> FP32
+    const uint64_t x_desc = tc::sw128_desc(tc::smem_u32(sX));
+    const uint32_t x_khalf = (uint32_t)BN * kRowBytes;     // second 64-element K half of an X image
+    bool ok = true;
+    for (int64_t j = 0; j < items && ok; ++j) {
+      bool w = !*vabort && tc::mbar_wait(&xfull, (uint32_t)(j & 1));
+      if (w) w = tc::mbar_wait(&accempty, (uint32_t)(j & 1) ^ 1u);
+      ok = __all_sync(0xffffffffu, w);
+      if (!ok) break;
+      tc::tc_fence_after();
 #pragma unroll
-            for (int kk = 0; kk < kNCP / 16; ++kk) {
-              const int kel = kk * 16;
-              const uint32_t aoff = (uint32_t)(kel >> 6) * kNCP * kRowBytes + (uint32_t)((kel & 63) * 2);
-              const uint32_t boff = (uint32_t)(kel >> 6) * BN * kRowBytes + (uint32_t)((kel & 63) * 2);
-              tc::mma_f16(d, tc::sw128_desc(a_base + aoff), tc::sw128_desc(x_base + boff), idesc,
+      for (int s = 0; s < S; ++s) {
+        const int64_t a = j * S + s;
+        const int q = (int)(a & 1);
+        w = !*vabort && tc::mbar_wait(&afull[q], (uint32_t)((a >> 1) & 1));
+        ok = __all_sync(0xffffffffu, w);
+        if (!ok) break;
+        tc::tc_fence_after();
+        // base descriptors plus compile-time offsets: a few integer adds per MMA
+        const uint64_t a0 = tc::sw128_desc(tc::smem_u32(sA + (size_t)q * kASlice));
+#pragma unroll
+        for (int t = 0; t < S - s; ++t) {
+          const uint32_t d = tmem + (uint32_t)((s + t) * BN);
+          const uint64_t x0 = tc::desc_add(x_desc, (uint32_t)t * x_bytes);
+          const uint64_t x1 = tc::desc_add(x0, x_khalf);
+#pragma unroll
+          for (int kk = 0; kk < kNCP / 16; ++kk) {
+            const int kel = kk * 16;
+            const uint32_t aoff = (uint32_t)(kel >> 6) * kNCP * kRowBytes + (uint32_t)((kel & 63) * 2);
+            const uint32_t boff = (uint32_t)((kel & 63) * 2);
+            if (leader)
+              tc::mma_f16(d, tc::desc_add(a0, aoff), tc::desc_add(kel < 64 ? x0 : x1, boff), idesc,
                           (s == 0 && kk == 0) ? 0u : 1u);
-            }
           }
-          tc::mma_commit(&aempty[q]);
         }
-        if (!ok) {
-          fail();
-          break;
-        }
+        __syncwarp();
+        if (leader) tc::mma_commit(&aempty[q]);
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (leader) {
         tc::mma_commit(&xempty);
         tc::mma_commit(&accfull);
       }
+      __syncwarp();
     }
-  } else if (warp < 13) {
-    // ---------------- epilogue: fold the 7 levels, scale, FP64 scatter-add
-    const int q = warp & 3;
+    if (!ok && leader) fail();
+  } else if (warp < 17) {
+    // ---------------- epilogue: fold the 7 levels, scale, FP64 scatter-add; two warps per TMEM
+    // lane quarter, alternate 16-column chunks each
+    const int q = warp & 3, hh = (warp - 9) >> 2;
     const int i = q * 32 + lane;
+    const int etid = (warp - 9) * 32 + lane;  // 0 .. 255
     for (int64_t j = 0; j < items; ++j) {
       const int64_t cell = blockIdx.x + (j / p.ntiles) * G;
       const int t = (int)(j % p.ntiles);
       bool ok = !*vabort && tc::mbar_wait(&accfull, (uint32_t)(j & 1));
       if (!ok) fail();
-      if (!__all_sync(0xffffffffu, ok && !*vabort)) break;
+      // column exponents of this tile, shared by the 8 epilogue warps
+      if (etid < BN) {
+        const int col = t * BN + etid;
+        int ex = col < p.n ? __ldg(p.cexp + col) : 0;
+        s_cexp[etid] = ex == -100000 ? 0 : ex;
+      }
+      // one decision for all 8 warps (named barrier 1 also publishes the exponents)
+      if (epi_any(!ok || *vabort)) break;
       tc::tc_fence_after();
       int g = -1, ea = 0;
       if (i < p.nc) {
@@ -284,11 +340,11 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
       }
       double* out = (g >= 0) ? p.Y + (int64_t)g * p.n : nullptr;
       const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float d0[16], hi[16], lo[16];
-        tc::tmem_ld16(lane_addr + (uint32_t)c0, d0);
+      for (int c0 = hh * 16; c0 < BN; c0 += 32) {
+        float hi[16], lo[16];
+        tc::tmem_ld16(lane_addr + (uint32_t)c0, hi);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) hi[u] = lo[u] = 0.f;
+        for (int u = 0; u < 16; ++u) lo[u] = 0.f;
         float scale = 0.00390625f;  // 2^-8
 #pragma unroll 1
         for (int L = 1; L < S; ++L) {
@@ -303,21 +359,21 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
           for (int u = 0; u < 16; ++u) {
             const int col = t * BN + c0 + u;
             if (col < p.n) {
-              int ex = __ldg(p.cexp + col);
-              if (ex == -100000) ex = 0;
-              const int pw = ea + ex - 16;
-              // level 0 is an exact integer below 2^24; levels 1..6 in float-float
-              const double v = f32_scaled(d0[u], pw) + (f32_scaled(hi[u], pw) + f32_scaled(lo[u], pw));
+              // (hi + lo) 2^(ea + ex - 16): two exact conversions by integer arithmetic, one FP64 add
+              const int pw = ea + s_cexp[c0 + u] - 16;
+              const double v = f32_scaled(hi[u], pw) + f32_scaled(lo[u], pw);
               atomicAdd(out + col, p.neg ? -v : v);
             }
           }
         }
       }
+      // the tile's exponents may be overwritten only after every epilogue warp is done with them
+      asm volatile("bar.sync 1, 256;" ::: "memory");
       tc::tc_fence_before();
       tc::mbar_arrive(&accempty);
     }
   } else {
-    // ---------------- cell-slice loader (warp 13, one lane)
+    // ---------------- cell-slice loader (warp 17, one lane)
     if (lane == 0) {
       int64_t issued = 0;
       for (int64_t j = 0; j < items && !*vabort; ++j) {

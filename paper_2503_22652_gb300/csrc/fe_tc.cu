@@ -216,45 +216,52 @@ __global__ void __launch_bounds__(kThreads, 1) fe_tc_kernel(const __grid_constan
       }
     }
   } else if (warp == 8) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      int64_t j = 0, cl = 0;
-      bool stop = false;
-      for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
-        const FePart& P = p.part[part_of(p, g)];
-        const int BN = P.BN;
-        const uint32_t idesc = tc::instr_desc(kFmt, kNCP, BN);
-        const int ab = (int)(cl & 1);
-        for (int t = 0; t < P.ntiles; ++t, ++j) {
-          const int bs = (int)(j & 1), xb = (int)(j & 1);
-          bool ok = !*vabort;
-          if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl >> 1) & 1));
-          if (ok) ok = tc::mbar_wait(&bfull[bs], (uint32_t)((j >> 1) & 1));
-          if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
-          if (!ok) {
-            fail();
-            stop = true;
-            break;
-          }
-          tc::tc_fence_after();
-          const uint32_t a_base = tc::smem_u32(sA[ab]);
-          const uint32_t b_base = tc::smem_u32(sB[bs]);
-          const uint32_t d = tmem + (uint32_t)(xb * p.maxBN);
-          constexpr int per = kRowBytes / ES;
+    // ---------------- MMA issuer: the whole warp walks the loops with warp-uniform values, one
+    // elected lane issues
+    const bool leader = tc::elect_one();
+    int64_t j = 0, cl = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
+      const FePart& P = p.part[part_of(p, g)];
+      const int BN = P.BN;
+      const uint32_t idesc = tc::instr_desc(kFmt, kNCP, BN);
+      const int ab = (int)(cl & 1);
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int bs = (int)(j & 1), xb = (int)(j & 1);
+        bool ok = !*vabort;
+        if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl >> 1) & 1));
+        if (ok) ok = tc::mbar_wait(&bfull[bs], (uint32_t)((j >> 1) & 1));
+        if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (leader) fail();
+          stop = true;
+          break;
+        }
+        tc::tc_fence_after();
+        // base descriptors plus compile-time offsets (one more add per 128-byte K block of B)
+        const uint64_t a0 = tc::sw128_desc(tc::smem_u32(sA[ab]));
+        const uint64_t b0 = tc::sw128_desc(tc::smem_u32(sB[bs]));
+        const uint32_t bblk = (uint32_t)BN * kRowBytes;
+        const uint32_t d = tmem + (uint32_t)(xb * p.maxBN);
+        constexpr int per = kRowBytes / ES;
 #pragma unroll
-          for (int kk = 0; kk < kNCP / KMMA; ++kk) {
-            const int kel = kk * KMMA;
-            const uint32_t aoff = (uint32_t)(kel / per) * kNCP * kRowBytes + (uint32_t)((kel % per) * ES);
-            const uint32_t boff = (uint32_t)(kel / per) * BN * kRowBytes + (uint32_t)((kel % per) * ES);
-            const uint64_t ad = tc::sw128_desc(a_base + aoff);
-            const uint64_t bd = tc::sw128_desc(b_base + boff);
+        for (int kk = 0; kk < kNCP / KMMA; ++kk) {
+          const int kel = kk * KMMA;
+          const uint32_t aoff = (uint32_t)(kel / per) * kNCP * kRowBytes + (uint32_t)((kel % per) * ES);
+          const uint64_t ad = tc::desc_add(a0, aoff);
+          const uint64_t bd = tc::desc_add(b0, (uint32_t)(kel / per) * bblk + (uint32_t)((kel % per) * ES));
+          if (leader) {
             if (BF16) tc::mma_f16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
             else tc::mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
           }
+        }
+        __syncwarp();
+        if (leader) {
           tc::mma_commit(&bempty[bs]);
           tc::mma_commit(&accfull[xb]);
           if (t == P.ntiles - 1) tc::mma_commit(&aempty[ab]);
         }
+        __syncwarp();
       }
     }
   } else if (warp < 13) {

@@ -194,49 +194,53 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
-      const uint32_t idesc = tc::instr_desc(1u, BM, BN);  // BF16 x BF16 -> FP32, M = 128, N = 32
-      for (int ci = 0; ci < nch; ++ci) {
-        const int b = ci & 1;
-        const int g = ci / GROUP, xb = g & 1;  // accumulation group and its TMEM buffer
-        const bool first = (ci % GROUP) == 0, last = (ci % GROUP) == GROUP - 1 || ci == nch - 1;
-        bool ok = !*vabort && tc::mbar_wait(&bfull[b], (uint32_t)((ci >> 1) & 1));
-        if (ok && first) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((g >> 1) & 1) ^ 1u);
-        if (!ok) {
-          fail();
-          break;
-        }
-        const uint32_t b_base = tc::smem_u32(sB + (size_t)b * kBBytes);
-        const uint32_t d_base = tmem + (uint32_t)(xb * S * BN);
-        for (int s = 0; s < S; ++s) {
-          const int j = ci * S + s;
-          const int q = j % ASTAGES;
-          if (*vabort || !tc::mbar_wait(&afull[q], (uint32_t)((j / ASTAGES) & 1))) {
-            ok = false;
-            break;
-          }
-          tc::tc_fence_after();
-          const uint32_t a_base = tc::smem_u32(sA + (size_t)q * kABytes);
-          for (int t = 0; t + s < S; ++t) {
-            const uint32_t d = d_base + (uint32_t)((s + t) * BN);
+    // ---------------- MMA issuer: the whole warp walks the fully unrolled (s, t, k) sequence with
+    // warp-uniform values, one elected lane issues
+    const bool leader = tc::elect_one();
+    const uint32_t idesc = tc::instr_desc(1u, BM, BN);  // BF16 x BF16 -> FP32, M = 128, N = 32
+    bool ok = true;
+    for (int ci = 0; ci < nch && ok; ++ci) {
+      const int b = ci & 1;
+      const int g = ci / GROUP, xb = g & 1;  // accumulation group and its TMEM buffer
+      const bool first = (ci % GROUP) == 0, last = (ci % GROUP) == GROUP - 1 || ci == nch - 1;
+      bool w = !*vabort && tc::mbar_wait(&bfull[b], (uint32_t)((ci >> 1) & 1));
+      if (w && first) w = tc::mbar_wait(&accempty[xb], (uint32_t)((g >> 1) & 1) ^ 1u);
+      ok = __all_sync(0xffffffffu, w);
+      if (!ok) break;
+      const uint64_t b_desc = tc::sw128_desc(tc::smem_u32(sB + (size_t)b * kBBytes));
+      const uint32_t d_base = tmem + (uint32_t)(xb * S * BN);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ad = tc::sw128_desc(a_base + kk * 32);
-              const uint64_t bd = tc::sw128_desc(b_base + (uint32_t)(t * BN * 128) + kk * 32);
-              tc::mma_f16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
-            }
-          }
-          tc::mma_commit(&aempty[q]);
+      for (int s = 0; s < S; ++s) {
+        const int j = ci * S + s;
+        const int q = j % ASTAGES;
+        w = !*vabort && tc::mbar_wait(&afull[q], (uint32_t)((j / ASTAGES) & 1));
+        ok = __all_sync(0xffffffffu, w);
+        if (!ok) break;
+        tc::tc_fence_after();
+        // base descriptors plus compile-time offsets: a few integer adds per MMA
+        const uint64_t a0 = tc::sw128_desc(tc::smem_u32(sA + (size_t)q * kABytes));
+#pragma unroll
+        for (int t = 0; t < S - s; ++t) {
+          const uint32_t d = d_base + (uint32_t)((s + t) * BN);
+          const uint64_t b0 = tc::desc_add(b_desc, (uint32_t)(t * BN * 128));
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (leader)
+              tc::mma_f16(d, tc::desc_add(a0, kk * 32), tc::desc_add(b0, kk * 32), idesc,
+                          (first && s == 0 && kk == 0) ? 0u : 1u);
         }
-        if (!ok) {
-          fail();
-          break;
-        }
+        __syncwarp();
+        if (leader) tc::mma_commit(&aempty[q]);
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (leader) {
         tc::mma_commit(&bempty[b]);
         if (last) tc::mma_commit(&accfull[xb]);
       }
+      __syncwarp();
     }
+    if (!ok && leader) fail();
   } else if (warp >= 4) {
     // ---------------- epilogue: 8 warps, lane quarter q, column half h
     const int q = warp & 3, h = (warp - 4) >> 2;

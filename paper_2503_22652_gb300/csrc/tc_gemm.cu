@@ -128,33 +128,42 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = *(volatile int*)&consumed; i < issued; ++i)
         tc::mbar_wait(&full_bar[i % kStages], (uint32_t)(i / kStages) & 1u);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: the whole warp walks the loop with warp-uniform values, one
+    // elected lane issues
+    const bool leader = tc::elect_one();
     const uint32_t idesc = tc::instr_desc(kFmt, kBM, BN);
     bool ok = true;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % kStages;
       const uint32_t ph = (uint32_t)(i / kStages) & 1u;
-      if (*vabort || !tc::mbar_wait(&full_bar[s], ph)) {
-        *vabort = 1;
-        atomicExch(err, 1);
+      const bool w = !*vabort && tc::mbar_wait(&full_bar[s], ph);
+      if (!__all_sync(0xffffffffu, w)) {
+        if (leader) {
+          *vabort = 1;
+          atomicExch(err, 1);
+        }
         ok = false;
         break;
       }
-      *(volatile int*)&consumed = i + 1;
+      if (leader) *(volatile int*)&consumed = i + 1;
       tc::tc_fence_after();
       const uint32_t a_base = tc::smem_u32(smem + (size_t)s * stage_bytes);
-      const uint32_t b_base = a_base + a_bytes;
+      const uint64_t a0 = tc::sw128_desc(a_base), b0 = tc::sw128_desc(a_base + a_bytes);
 #pragma unroll
       for (int kk = 0; kk < BK / KMMA; ++kk) {
-        const uint64_t ad = tc::sw128_desc(a_base + kk * 32);
-        const uint64_t bd = tc::sw128_desc(b_base + kk * 32);
-        if (kBF16) tc::mma_f16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-        else tc::mma_tf32(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        const uint64_t ad = tc::desc_add(a0, kk * 32);
+        const uint64_t bd = tc::desc_add(b0, kk * 32);
+        if (leader) {
+          if (kBF16) tc::mma_f16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          else tc::mma_tf32(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        }
       }
-      tc::mma_commit(&empty_bar[s]);
+      __syncwarp();
+      if (leader) tc::mma_commit(&empty_bar[s]);
+      __syncwarp();
     }
-    if (ok) tc::mma_commit(&acc_bar);
+    if (ok && leader) tc::mma_commit(&acc_bar);
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM -> registers -> global
     const int q = warp & 3;  // TMEM lane quarter this warp may access

@@ -144,6 +144,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
   return d;
 }
 
+// One lane of a converged warp (elect.sync): the MMA issuers run their loops on the whole warp so
+// that every loop value stays warp-uniform, and only the elected lane issues.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t e;
+  asm volatile("{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\tselp.u32 %0, 1, 0, p;\n\t}" : "=r"(e));
+  return e != 0;
+}
+
+// The descriptor of a tile `bytes` further on: the start-address field is the shared-memory
+// address / 16 in the low 14 bits, and shared-memory addresses stay below 256 KB, so the offset
+// adds without a carry.  (One 64-bit add per MMA instead of rebuilding the descriptor.)
+__device__ __forceinline__ uint64_t desc_add(uint64_t desc, uint32_t bytes) { return desc + (uint64_t)(bytes >> 4); }
+
 // Instruction descriptor: D = F32, A/B format `fmt` (kind::f16: 1 = BF16; kind::tf32: 2 = TF32),
 // both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int M, int N) {
