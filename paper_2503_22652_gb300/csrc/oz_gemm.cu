@@ -46,13 +46,30 @@ __global__ void rowexp_kcontig(int64_t R, int64_t K, const double* __restrict__ 
   if (lane == 0) ex[r] = (e == -100000) ? 0 : e;
 }
 
-// Row exponents, rows contiguous across threads (element (r, k) at X[r + k * ks]): thread per row.
-__global__ void rowexp_rcontig(int64_t R, int64_t K, const double* __restrict__ X, int64_t ks, int* ex) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+// Row exponents, rows contiguous across threads (element (r, k) at X[r + k * ks]): 32 rows per
+// block (coalesced), the K range split over the block's 8 warps and over blockIdx.y.  Partial maxima
+// meet in ex by atomicMax (ex preset to INT_MIN); rowexp_fix then maps rows without a nonzero
+// element to 0.
+__global__ void __launch_bounds__(256) rowexp_rcontig(int64_t R, int64_t K, const double* __restrict__ X, int64_t ks,
+                                                      int* ex) {
+  __shared__ int red[8][32];
+  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
   int e = -100000;
-  for (int64_t k = 0; k < K; ++k) e = max(e, exp_of(X[r + k * ks]));
-  ex[r] = (e == -100000) ? 0 : e;
+  if (r < R)
+    for (int64_t k = threadIdx.y + 8 * (int64_t)blockIdx.y; k < K; k += 8 * (int64_t)gridDim.y)
+      e = max(e, exp_of(X[r + k * ks]));
+  red[threadIdx.y][threadIdx.x] = e;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < R) {
+#pragma unroll
+    for (int y = 1; y < 8; ++y) e = max(e, red[y][threadIdx.x]);
+    atomicMax(ex + r, e);
+  }
+}
+
+__global__ void rowexp_fix(int64_t R, int* ex) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < R && ex[r] <= -100000) ex[r] = 0;
 }
 
 // Slices of a 32-row x 64-k tile.  Block (32, 8).
@@ -336,6 +353,18 @@ CUtensorMap slice_map(const OzOperand& op, int box_rows) {
 
 }  // namespace
 
+namespace {
+int sm_count() {
+  static const int n = [] {
+    int d = 0, c = 152;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+      c = 152;
+    return c;
+  }();
+  return n;
+}
+}  // namespace
+
 void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs, int64_t ks, OzOperand& op) {
   RC_CHECK(R > 0 && K > 0, RCHFSI_ERR_INVALID_ARG, "oz_slice: empty operand");
   RC_CHECK(ks == 1 || rs == 1, RCHFSI_ERR_INVALID_ARG, "oz_slice: one of the strides must be 1");
@@ -350,7 +379,13 @@ void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs,
   if (ks == 1) {
     rowexp_kcontig<<<cdiv(R, 8), 256, 0, s>>>(R, K, X, rs, op.ex.p);
   } else {
-    rowexp_rcontig<<<cdiv(R, 256), 256, 0, s>>>(R, K, X, ks, op.ex.p);
+    // enough blocks to fill the GPU a few times over, each warp walking at least 8 k
+    const unsigned rb = cdiv(R, 32);
+    const unsigned kb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(K, 64), (int64_t)(sm_count() * 16) / rb));
+    RC_CUDA(cudaMemsetAsync(op.ex.p, 0x80, sizeof(int) * R, s));  // 0x80808080: below every exponent
+    rowexp_rcontig<<<dim3(rb, kb), dim3(32, 8), 0, s>>>(R, K, X, ks, op.ex.p);
+    RC_LAUNCH();
+    rowexp_fix<<<cdiv(R, 256), 256, 0, s>>>(R, op.ex.p);
   }
   RC_LAUNCH();
   RC_CHECK(cdiv(R, 32) <= 65535u, RCHFSI_ERR_INVALID_ARG, "oz_slice: too many rows");

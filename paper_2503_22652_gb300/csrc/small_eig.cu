@@ -8,9 +8,12 @@
 //   * chol_inv_kernel: right-looking Cholesky G = L L^T (one barrier per column), then L^-1 column
 //     by column (each column of L^-1 is an independent forward substitution, owned by one warp);
 //   * tridiag_kernel: Householder reduction to tridiagonal form Q^T M Q = T (two barriers per
-//     column: after the symmetric matrix-vector product, after the rank-2 update);
+//     column: after the symmetric matrix-vector product, after the rank-2 update); for one cluster,
+//     tridiag_dsmem_kernel exchanges through distributed shared memory and has the owner of the
+//     next pivot column compute its Householder scalars during the update;
 //   * bisect_kernel: eigenvalues of T by Sturm-sequence multisection, one warp per eigenvalue
-//     (32 trial points per step);
+//     (32 trial points per step), the Sturm recurrence free of per-step checks (exact zeros are
+//     detected off the dependency chain and only then recounted with the substitution);
 //   * inviter_kernel: eigenvectors of T by inverse iteration (tridiagonal LU with partial pivoting),
 //     Gram-Schmidt inside clusters of numerically equal eigenvalues (gap <= 1e-9 ||T||), then one
 //     Newton-Schulz step Z <- Z (3 I - Z^T Z) / 2 (two GEMMs) for the O(eps ||T|| / gap) residue
@@ -62,6 +65,67 @@ __device__ double block_sum(double v, double* red) {
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Two warp sums with their shuffle / add latencies interleaved.
+__device__ __forceinline__ void warp_sum2(double& a, double& b) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ta = __shfl_xor_sync(0xffffffffu, a, o), tb = __shfl_xor_sync(0xffffffffu, b, o);
+    a += ta;
+    b += tb;
+  }
+}
+
+// The loops below walk rows in warp-uniform chunks of 32, four chunks per iteration with all loads
+// issued before the FMAs: an FP64 FMA has ~64 clocks of latency, so a load-FMA-store chain per
+// element leaves the FP64 pipe idle, while a chunk that lies past the end is skipped as a whole (on
+// this GPU a warp-wide FP64 instruction occupies the SM's FP64 pipe for ~12 clocks whatever its
+// active lanes, so the FMA count must stay that of the plain loop).
+// Lane partial of sum_{i < rr} mc[i] v[i].
+__device__ __forceinline__ double dot_part(const double* mc, const double* v, int rr, int lane) {
+  double a0 = 0.0, a1 = 0.0;
+  for (int c0 = 0; c0 < rr; c0 += 128) {
+    double m[4], x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = c0 + 32 * u + lane;
+      m[u] = i < rr ? mc[i] : 0.0;
+      x[u] = i < rr ? v[i] : 0.0;
+    }
+    if (c0 < rr) a0 = fma(m[0], x[0], a0);
+    if (c0 + 32 < rr) a1 = fma(m[1], x[1], a1);
+    if (c0 + 64 < rr) a0 = fma(m[2], x[2], a0);
+    if (c0 + 96 < rr) a1 = fma(m[3], x[3], a1);
+  }
+  return a0 + a1;
+}
+
+// mc[i] -= v[i] wc + w[i] vc for i < rr; with S2, also the lane partial of sum_{i >= 2} mc[i]^2 of
+// the new values.
+template <bool S2>
+__device__ __forceinline__ double rank2_part(double* mc, const double* v, const double* w, double vc, double wc,
+                                             int rr, int lane) {
+  double s2 = 0.0;
+  for (int c0 = 0; c0 < rr; c0 += 128) {
+    double m[4], x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = c0 + 32 * u + lane;
+      m[u] = i < rr ? mc[i] : 0.0;
+      x[u] = i < rr ? v[i] : 0.0;
+      y[u] = i < rr ? w[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (c0 + 32 * u < rr) {
+        const int i = c0 + 32 * u + lane;
+        const double nm = fma(-y[u], vc, fma(-x[u], wc, m[u]));
+        if (i < rr) mc[i] = nm;
+        if (S2) s2 = fma(i >= 2 && i < rr ? nm : 0.0, nm, s2);
+      }
+    }
+  }
+  return s2;
 }
 
 // ------------------------------------------------------------------ Cholesky and L^-1
@@ -398,6 +462,169 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_smem_kernel(int n, const 
   if ((n - 1) % P == r && tid == 0) d[n - 1] = cols[(size_t)((n - 1 - r) / P) * n + n - 1];
 }
 
+// The same reduction for one thread-block cluster, with every exchange through distributed shared
+// memory instead of L2.  All CTAs use one layout (nqm = ceil(n / P) column slots), so a remote
+// address is the local one in another rank.  The owner of column k + 1 updates that column first
+// (warp 0) and, while its other warps finish the rank-2 update, computes the Householder scalars of
+// the next step (alpha, beta, tau and the scale 1 / (alpha - beta)) and keeps them with the column;
+// the other CTAs read them after the barrier instead of each recomputing the norm, the square root
+// and the divide.  Step k: read pivot column k and its scalars from the owner -> own products
+// t (A v)_c -> barrier -> read the products p_c of all CTAs -> rank-2 update -> barrier.  The loop
+// writes nothing to global memory (a barrier's release then has no stores to wait for); H, d, e
+// and tau are written at the end from the owned columns and their scalars.
+constexpr int TRI_DS_SLOTS = 8;  // per owned column: beta, tau, scale, diagonal (4 used)
+
+size_t tridiag_dsmem_smem(int n, int P) {
+  const size_t nqm = ((size_t)n + P - 1) / P;
+  return (nqm * n + 2 * (size_t)n + nqm * (1 + TRI_DS_SLOTS) + 40) * sizeof(double);
+}
+
+// Householder scalars of x = column c rows c+1.. (alpha = x_0, xn2 = |x_1..|^2), as in tridiag_smem_kernel.
+__device__ __forceinline__ void house_scalars(double alpha, double xn2, double* beta, double* t, double* sc) {
+  *beta = alpha;
+  *t = 0.0;
+  *sc = 1.0;
+  if (xn2 > 0.0) {
+    const double b = -copysign(sqrt(alpha * alpha + xn2), alpha);
+    const double g = alpha - b, rcp = 1.0 / (b * g);
+    *beta = b;
+    *t = -(g * g) * rcp;
+    *sc = b * rcp;
+  }
+}
+
+__global__ void __launch_bounds__(TRI_THREADS) tridiag_dsmem_kernel(int n, const double* __restrict__ Min, double* H,
+                                                                    double* d, double* e, double* tau) {
+  extern __shared__ double sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int P = (int)cluster.num_blocks(), r = (int)cluster.block_rank();
+  const int nqm = (n + P - 1) / P;
+  const int nq = (n - r + P - 1) / P;  // owned columns c = r + q P, q < nq
+  double* cols = sm;                          // nqm x n
+  double* v = cols + (size_t)nqm * n;         // n
+  double* w = v + n;                          // n
+  double* prod = w + n;                       // nqm: t (A v)_c of the owned columns
+  double* hs = prod + nqm;                    // nqm x TRI_DS_SLOTS: beta, tau, scale, diagonal
+  double* red = hs + (size_t)nqm * TRI_DS_SLOTS;  // 33
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int q = 0; q < nq; ++q)
+    for (int i = tid; i < n; i += blockDim.x) cols[(size_t)q * n + i] = Min[(size_t)(r + q * P) * n + i];
+  __syncthreads();
+  // scalars of pivot column 0 (owner: rank 0)
+  if (r == 0 && warp == 0 && n > 2) {
+    double s2 = 0.0;
+    for (int i = 2 + lane; i < n; i += 32) s2 += cols[i] * cols[i];
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      house_scalars(cols[1], s2, hs + 0, hs + 1, hs + 2);
+      hs[3] = cols[0];
+    }
+  }
+  cluster.sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int rr = n - k - 1;
+    const int ok_ = k % P, oq = k / P;  // owner of the pivot column and its slot
+    const double* pc = cluster.map_shared_rank(cols + (size_t)oq * n, ok_);
+    const double* ph = cluster.map_shared_rank(hs + (size_t)oq * TRI_DS_SLOTS, ok_);
+    // v = (1, x_1 sc, x_2 sc, ...) from the owner's column (the loads are issued together)
+    double xv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = tid + (int)blockDim.x * u;
+      xv[u] = (i > 0 && i < rr) ? pc[k + 1 + i] : 0.0;
+    }
+    const double t = ph[1], sc = ph[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = tid + (int)blockDim.x * u;
+      if (i < rr) v[i] = i == 0 ? 1.0 : xv[u] * sc;
+    }
+    for (int i = tid + 2 * (int)blockDim.x; i < rr; i += blockDim.x) v[i] = pc[k + 1 + i] * sc;
+    __syncthreads();
+    const int qa = (k + 1 - r + P - 1) / P > 0 ? (k + 1 - r + P - 1) / P : 0;
+    if (t != 0.0) {
+      // owned columns in pairs per warp, the two reductions interleaved
+      for (int q = qa + warp; q < nq; q += 2 * nw) {
+        const int q2 = q + nw;
+        double a = dot_part(cols + (size_t)q * n + k + 1, v, rr, lane);
+        double b = q2 < nq ? dot_part(cols + (size_t)q2 * n + k + 1, v, rr, lane) : 0.0;
+        warp_sum2(a, b);
+        if (lane == 0) {
+          prod[q] = t * a;
+          if (q2 < nq) prod[q2] = t * b;
+        }
+      }
+    }
+    cluster.sync();
+    // the owner of column k + 1 computes the next scalars; its warp 0 updates only that column
+    const bool next_owner = (k + 1) % P == r && k + 3 < n;
+    if (t != 0.0) {
+      for (int i = tid; i < rr; i += blockDim.x) {
+        const int c = k + 1 + i;
+        w[i] = cluster.map_shared_rank(prod, c % P)[c / P];
+      }
+      __syncthreads();
+      double pv = 0.0;
+      for (int i = tid; i < rr; i += blockDim.x) pv += w[i] * v[i];
+      const double K = -0.5 * t * block_sum(pv, red);
+      for (int i = tid; i < rr; i += blockDim.x) w[i] += K * v[i];
+      __syncthreads();
+      if (next_owner && warp == 0) {
+        const int q = qa;  // column k + 1
+        double* col = cols + (size_t)q * n;
+        double s2 = rank2_part<true>(col + k + 1, v, w, v[0], w[0], rr, lane);
+        s2 = warp_sum(s2);
+        __syncwarp();
+        if (lane == 0) {
+          double* h = hs + (size_t)q * TRI_DS_SLOTS;
+          house_scalars(col[k + 2], s2, h + 0, h + 1, h + 2);
+          h[3] = col[k + 1];
+        }
+      } else {
+        const int q0 = next_owner ? qa + 1 : qa, w0 = next_owner ? 1 : 0, ws = nw - w0;
+        for (int q = q0 + (warp - w0); q < nq; q += ws) {
+          const int c = r + q * P;
+          rank2_part<false>(cols + (size_t)q * n + k + 1, v, w, v[c - k - 1], w[c - k - 1], rr, lane);
+        }
+      }
+    } else if (next_owner && warp == 0) {
+      // no update this step: column k + 1 as it stands
+      const int q = qa;
+      const double* col = cols + (size_t)q * n;
+      double s2 = 0.0;
+      for (int i = k + 3 + lane; i < n; i += 32) s2 += col[i] * col[i];
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        double* h = hs + (size_t)q * TRI_DS_SLOTS;
+        house_scalars(col[k + 2], s2, h + 0, h + 1, h + 2);
+        h[3] = col[k + 1];
+      }
+    }
+    cluster.sync();
+  }
+  // outputs of the owned pivot columns k < n - 2: d, e, tau and H(:, k) = (1, x sc)
+  for (int q = 0; q < nq; ++q) {
+    const int k = r + q * P;
+    if (k + 2 >= n) break;
+    const double* col = cols + (size_t)q * n;
+    const double* h = hs + (size_t)q * TRI_DS_SLOTS;
+    const double sc = h[2];
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) H[(int64_t)k * n + i] = i == k + 1 ? 1.0 : col[i] * sc;
+    if (tid == 0) {
+      d[k] = h[3];
+      e[k] = h[0];
+      tau[k] = h[1];
+    }
+  }
+  // last 2 x 2 block
+  if (n >= 2 && (n - 2) % P == r && tid == 0) {
+    const double* mc = cols + (size_t)((n - 2 - r) / P) * n;
+    d[n - 2] = mc[n - 2];
+    e[n - 2] = mc[n - 1];
+  }
+  if ((n - 1) % P == r && tid == 0) d[n - 1] = cols[(size_t)((n - 1 - r) / P) * n + n - 1];
+}
+
 // ------------------------------------------------------------------ tridiagonal eigenvalues
 // Number of eigenvalues of T below x: sign changes of the Sturm sequence of leading principal
 // minors p_i = det(T_i - x I), by the three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}
@@ -460,6 +687,48 @@ __device__ void sturm_count_k(int n, const double* ds, const double* e2s, const 
 // pipe for ~12 clocks, so more sequences per lane trade latency for pipe time at a loss (measured).
 constexpr int kChains = 1;
 
+// The same count without the per-step zero substitution, so that the dependency chain from one
+// minor to the next is the FMA alone: sign changes are read from the high words and accumulated
+// off the chain, and *zero is set when a minor came out exactly zero (or with a zero high word, a
+// subnormal below 2^-1042), the one case in which the substitution would have changed the count.
+// The caller then recounts that shift with sturm_count_k.
+__device__ __forceinline__ int sturm_count_fast(int n, const double* ds, const double* e2s, double xs, bool* zero) {
+  double pm = 1.0, p = ds[0] - xs;
+  uint32_t hp = (uint32_t)__double2hiint(p);
+  int cnt = (int)(hp >> 31);
+  uint32_t zmin = hp << 1;  // zero iff some minor had a zero high word (sign bit dropped)
+  int i = 1;
+  for (; i + 8 <= n; i += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double pn = fma(ds[i + u] - xs, p, -e2s[i + u] * pm);
+      const uint32_t hn = (uint32_t)__double2hiint(pn);
+      cnt += (int)((hn ^ hp) >> 31);
+      zmin = min(zmin, hn << 1);
+      pm = p;
+      p = pn;
+      hp = hn;
+    }
+    // rescale the pair by a power of two (signs and ratios unchanged)
+    const uint32_t ep = ((uint32_t)__double2hiint(p) >> 20) & 0x7ffu, eq = ((uint32_t)__double2hiint(pm) >> 20) & 0x7ffu;
+    const int ex = (int)(ep > eq ? ep : eq) - 1023;
+    const double sc = __hiloint2double((1023 - ex) << 20, 0);
+    p *= sc;
+    pm *= sc;
+  }
+  for (; i < n; ++i) {
+    const double pn = fma(ds[i] - xs, p, -e2s[i] * pm);
+    const uint32_t hn = (uint32_t)__double2hiint(pn);
+    cnt += (int)((hn ^ hp) >> 31);
+    zmin = min(zmin, hn << 1);
+    pm = p;
+    p = pn;
+    hp = hn;
+  }
+  *zero = zmin == 0u;
+  return cnt;
+}
+
 // Eigenvalue j (ascending) of T = tridiag(e, d, e): one warp (one CTA), 32 kChains trial points per step.
 __global__ void __launch_bounds__(32) bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                                                     double* lam, double* tnorm_out) {
@@ -502,7 +771,9 @@ __global__ void __launch_bounds__(32) bisect_kernel(int n, const double* __restr
       x[c] = lo + w * (double)(c * 32 + lane + 1);
       xs[c] = x[c] * inv_tn;
     }
-    sturm_count_k<kChains>(n, ds, e2s, xs, cnt);
+    bool zero = false;
+    cnt[0] = sturm_count_fast(n, ds, e2s, xs[0], &zero);
+    if (zero) sturm_count_k<1>(n, ds, e2s, xs, cnt);
     // counts grow with x, so the first point with count > j bounds the eigenvalue from above
     int q = -1;
 #pragma unroll
@@ -840,6 +1111,17 @@ bool launch_resident(cudaStream_t s, void (*kc)(Args...), void (*kg)(Args...), i
   return true;
 }
 
+// One cluster of tridiag_dsmem_kernel when its CTAs hold the owned columns; false otherwise.
+bool launch_tridiag_dsmem(cudaStream_t s, int n, const double* M, double* H, double* d, double* e, double* tau) {
+  static const int csz = cluster_size_for(reinterpret_cast<const void*>(tridiag_dsmem_kernel), TRI_THREADS, SMEM_CAP);
+  if (csz <= 0 || tridiag_dsmem_smem(n, csz) > SMEM_CAP) return false;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = cluster_cfg(csz, TRI_THREADS, tridiag_dsmem_smem(n, csz), s, at);
+  RC_CUDA(cudaLaunchKernelEx(&cfg, tridiag_dsmem_kernel, n, M, H, d, e, tau));
+  RC_LAUNCH();
+  return true;
+}
+
 template <int R>
 void launch_backtransform(cudaStream_t s, int n, const double* H, const double* tau, double* V) {
   backtransform_reg_kernel<R><<<cdiv(n, 2), 64, 0, s>>>(n, H, tau, V);
@@ -884,7 +1166,8 @@ bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, Dev
   RC_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, s));
   RC_CUDA(cudaMemsetAsync(tau, 0, sizeof(double) * n, s));
   // 1. Q^T M Q = T
-  if (!launch_resident(s, tridiag_smem_kernel<true>, tridiag_smem_kernel<false>, n, num_sms, n, (const double*)M, H,
+  if (!launch_tridiag_dsmem(s, n, M, H, d, e, tau) &&
+      !launch_resident(s, tridiag_smem_kernel<true>, tridiag_smem_kernel<false>, n, num_sms, n, (const double*)M, H,
                        d, e, tau, xch, p))
     launch_multi(s, tridiag_kernel<true>, tridiag_kernel<false>, n, num_sms, n, M, H, d, e, tau, p);
   // 2. eigenvalues of T
