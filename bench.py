@@ -558,7 +558,11 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     prob = make_problem(args.workload)
     m, N = prob["m"], prob["block"]
-    stream = torch.cuda.current_stream()
+    # one non-default stream for torch's work and the library's (the handle of the legacy default
+    # stream would read as NULL, a library-owned stream): the CUDA events below then bracket
+    # exactly the library's work, and torch's writes to the inputs are ordered before it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     s = Solver(m, nev=prob["nev"], block=N, degree=prob["degree"], precision=args.precision, max_iter=200,
                tol=prob["tol"], stream=stream.cuda_stream, rr_mode=args.rr, eig_mode=args.eig)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731

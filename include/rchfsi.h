@@ -19,8 +19,11 @@
  *     the library detects which (cudaPointerGetAttributes) and stages host data through its own
  *     device buffers.  The caller owns all argument buffers; the library copies what it keeps.
  *   - Calls on one handle are serialised on the handle's CUDA stream and return after the result
- *     is complete (the stream is synchronised before returning).  A handle must not be used by
- *     two host threads at once.  Different handles are independent.
+ *     is complete (the stream is synchronised before returning).  Device inputs are read on that
+ *     stream: work that writes them on another stream (including the legacy default stream,
+ *     which a library-owned non-blocking stream does not wait for) must be complete before the
+ *     call.  A handle must not be used by two host threads at once.  Different handles are
+ *     independent.
  *   - Complex Hermitian problems (field = RCHFSI_COMPLEX, e.g. the Bloch k-point operators of
  *     Section 4.2) take complex blocks X, W, Y_p, the dense A and the cell matrices A_cells as
  *     interleaved (re, im) pairs of doubles, i.e. C99 `double complex` / NumPy complex128 arrays of

@@ -59,6 +59,11 @@ def _check_arr(a, shape, name, dtype=np.float64):
         raise ValueError("%s: expected a %s tensor" % (name, np.dtype(dtype).name))
     if a.numel() != int(np.prod(shape)):
         raise ValueError("%s: expected %s elements" % (name, int(np.prod(shape))))
+    if a.is_cuda:
+        # the library reads device inputs on its own stream: torch's pending writes to this tensor
+        # (a clone, a copy from the host) must have landed first
+        import torch
+        torch.cuda.current_stream(a.device).synchronize()
     return a
 
 
