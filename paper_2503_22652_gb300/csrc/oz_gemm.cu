@@ -402,7 +402,23 @@ void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B
   const int m_tiles = (int)((M + BM - 1) / BM), n_tiles = (int)((N + BN - 1) / BN);
   const int nchunks = (int)(A.Kp / KC);
   const int tiles = m_tiles * n_tiles;
-  int nsplit = std::max(1, std::min(nchunks, num_sms / std::max(tiles, 1)));
+  // split-K count: the smallest with which the CTAs fill whole waves of one CTA per SM to >= 90%
+  // (else the best found), each split keeping >= 4 chunks so that its TMEM drains stay amortised
+  int nsplit = 1;
+  {
+    const int max_split = std::max(1, std::min(64, nchunks / 4));
+    double best = -1.0;
+    for (int ns = 1; ns <= max_split; ++ns) {
+      const int64_t ctas = (int64_t)tiles * ns;
+      const int64_t waves = (ctas + num_sms - 1) / num_sms;
+      const double eff = (double)ctas / (double)(waves * num_sms);
+      if (eff > best + 1e-9) {
+        best = eff;
+        nsplit = ns;
+      }
+      if (eff >= 0.9) break;
+    }
+  }
   const int per = (nchunks + nsplit - 1) / nsplit;
   nsplit = (nchunks + per - 1) / per;
   RC_CHECK(m_tiles <= 65535 && nsplit <= 65535, RCHFSI_ERR_INVALID_ARG, "oz_gemm: grid too large");
