@@ -23,7 +23,6 @@ namespace {
 
 constexpr int S = kOzSlices;
 constexpr int BM = 128;
-constexpr int BN = 32;
 constexpr int KC = 64;            // K chunk: one 128-byte row of BF16
 // Chunks accumulated in TMEM before a drain: 2 x 64 = 128 K terms per exact FP32 sum (each term a
 // product of two integer slices, |t_s t_r| <= 2^16, so every partial sum stays below 2^23).
@@ -31,8 +30,15 @@ constexpr int GROUP = 2;
 constexpr int ASTAGES = 6;
 constexpr int kThreads = 384;     // 12 warps
 constexpr uint32_t kABytes = BM * 128;       // 16 KB per A slice tile
-constexpr uint32_t kBBytes = S * BN * 128;   // 28 KB: all B slices of one chunk
-constexpr uint32_t kTmemCols = 512;          // 2 buffers x 7 levels x 32 columns = 448
+constexpr uint32_t kTmemCols = 512;          // 7 levels x 32 columns x 2 buffers, or x 64 x 1 = 448
+// Output tile BM x BN: BN = 32 with two TMEM accumulator buffers (the drain of one group overlaps
+// the products of the next), or BN = 64 with one (each MMA carries twice the columns for 4/3 of the
+// shared-memory operand traffic; the MMAs wait for each drain).
+template <int BN>
+struct OzTile {
+  static constexpr int NBUF = BN == 32 ? 2 : 1;
+  static constexpr uint32_t kBBytes = S * BN * 128;  // all B slices of one chunk: 28 / 56 KB
+};
 
 // ---------------------------------------------------------------- slicing
 // Row exponents, K-contiguous rows: one warp per row.
@@ -135,8 +141,11 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
   lo += e;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, OzArgs p) {
+  constexpr int NBUF = OzTile<BN>::NBUF;
+  constexpr uint32_t kBBytes = OzTile<BN>::kBBytes;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t afull[ASTAGES], aempty[ASTAGES], bfull[2], bempty[2], accfull[2], accempty[2];
   __shared__ uint32_t tmem_slot;
@@ -214,14 +223,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer: the whole warp walks the fully unrolled (s, t, k) sequence with
     // warp-uniform values, one elected lane issues
     const bool leader = tc::elect_one();
-    const uint32_t idesc = tc::instr_desc(1u, BM, BN);  // BF16 x BF16 -> FP32, M = 128, N = 32
+    const uint32_t idesc = tc::instr_desc(1u, BM, BN);  // BF16 x BF16 -> FP32, M = 128
     bool ok = true;
     for (int ci = 0; ci < nch && ok; ++ci) {
       const int b = ci & 1;
-      const int g = ci / GROUP, xb = g & 1;  // accumulation group and its TMEM buffer
+      const int g = ci / GROUP, xb = g % NBUF;  // accumulation group and its TMEM buffer
       const bool first = (ci % GROUP) == 0, last = (ci % GROUP) == GROUP - 1 || ci == nch - 1;
       bool w = !*vabort && tc::mbar_wait(&bfull[b], (uint32_t)((ci >> 1) & 1));
-      if (w && first) w = tc::mbar_wait(&accempty[xb], (uint32_t)((g >> 1) & 1) ^ 1u);
+      if (w && first) w = tc::mbar_wait(&accempty[xb], (uint32_t)((g / NBUF) & 1) ^ 1u);
       ok = __all_sync(0xffffffffu, w);
       if (!ok) break;
       const uint64_t b_desc = tc::sw128_desc(tc::smem_u32(sB + (size_t)b * kBBytes));
@@ -259,30 +268,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (!ok && leader) fail();
   } else if (warp >= 4) {
-    // ---------------- epilogue: 8 warps, lane quarter q, column half h
+    // ---------------- epilogue: 8 warps, lane quarter q, column half h (BN / 2 columns each)
+    constexpr int HC = BN / 2;
     const int q = warp & 3, h = (warp - 4) >> 2;
-    float hi[16], lo[16];
+    float hi[HC], lo[HC];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) hi[u] = lo[u] = 0.f;
+    for (int u = 0; u < HC; ++u) hi[u] = lo[u] = 0.f;
     bool ok = true;
     const int ngroups = (nch + GROUP - 1) / GROUP;
     for (int g = 0; g < ngroups; ++g) {
-      const int b = g & 1;
-      bool w = !*vabort && tc::mbar_wait(&accfull[b], (uint32_t)((g >> 1) & 1));
+      const int b = g % NBUF;
+      bool w = !*vabort && tc::mbar_wait(&accfull[b], (uint32_t)((g / NBUF) & 1));
       if (!w) fail();
       if (!__all_sync(0xffffffffu, w && !*vabort)) {
         ok = false;
         break;
       }
       tc::tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * S * BN + h * 16);
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * S * BN + h * HC);
       float scale = 1.f;
 #pragma unroll 1
       for (int L = 0; L < S; ++L) {
-        float v[16];
-        tc::tmem_ld16(base + (uint32_t)(L * BN), v);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) two_sum(hi[u], lo[u], v[u] * scale);
+        for (int c = 0; c < HC / 16; ++c) {
+          float v[16];
+          tc::tmem_ld16(base + (uint32_t)(L * BN + c * 16), v);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) two_sum(hi[c * 16 + u], lo[c * 16 + u], v[u] * scale);
+        }
         scale *= 0.00390625f;  // 2^-8
       }
       tc::tc_fence_before();
@@ -293,8 +306,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (i < p.M) {
         const int ei = p.ea[i];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int64_t jcol = (int64_t)n0 + h * 16 + u;
+        for (int u = 0; u < HC; ++u) {
+          const int64_t jcol = (int64_t)n0 + h * HC + u;
           if (jcol < p.N) {
             const double v = ldexp((double)hi[u] + (double)lo[u], ei + p.eb[jcol] - 16);
             if (p.partial) p.C[((int64_t)split * p.N + jcol) * p.M + i] = v;
@@ -394,38 +407,46 @@ void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs,
   RC_LAUNCH();
 }
 
-void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
-             DevBuf<double>& ws, int* err) {
-  RC_CHECK(A.K == B.K && A.Kp == B.Kp, RCHFSI_ERR_INVALID_ARG, "oz_gemm: K mismatch");
+namespace {
+
+// Split-K count: the smallest with which the CTAs fill whole waves of one CTA per SM to >= 90%
+// (else the best found), each split keeping >= 4 chunks so that its TMEM drains stay amortised.
+int choose_split(int tiles, int nchunks, int num_sms, double* eff_out) {
+  const int max_split = std::max(1, std::min(64, nchunks / 4));
+  double best = -1.0;
+  int nsplit = 1;
+  for (int ns = 1; ns <= max_split; ++ns) {
+    const int64_t ctas = (int64_t)tiles * ns;
+    const int64_t waves = (ctas + num_sms - 1) / num_sms;
+    const double eff = (double)ctas / (double)(waves * num_sms);
+    if (eff > best + 1e-9) {
+      best = eff;
+      nsplit = ns;
+    }
+    if (eff >= 0.9) break;
+  }
+  *eff_out = best;
+  return nsplit;
+}
+
+template <int BN>
+void oz_gemm_launch(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
+                    DevBuf<double>& ws, int* err, int nsplit_in) {
   const int64_t M = A.R, N = B.R;
-  RC_CHECK(M < (1LL << 31) && N < (1LL << 31), RCHFSI_ERR_INVALID_ARG, "oz_gemm: too large");
   const int m_tiles = (int)((M + BM - 1) / BM), n_tiles = (int)((N + BN - 1) / BN);
   const int nchunks = (int)(A.Kp / KC);
-  const int tiles = m_tiles * n_tiles;
-  // split-K count: the smallest with which the CTAs fill whole waves of one CTA per SM to >= 90%
-  // (else the best found), each split keeping >= 4 chunks so that its TMEM drains stay amortised
-  int nsplit = 1;
-  {
-    const int max_split = std::max(1, std::min(64, nchunks / 4));
-    double best = -1.0;
-    for (int ns = 1; ns <= max_split; ++ns) {
-      const int64_t ctas = (int64_t)tiles * ns;
-      const int64_t waves = (ctas + num_sms - 1) / num_sms;
-      const double eff = (double)ctas / (double)(waves * num_sms);
-      if (eff > best + 1e-9) {
-        best = eff;
-        nsplit = ns;
-      }
-      if (eff >= 0.9) break;
-    }
-  }
+  int nsplit = nsplit_in;
   const int per = (nchunks + nsplit - 1) / nsplit;
   nsplit = (nchunks + per - 1) / per;
   RC_CHECK(m_tiles <= 65535 && nsplit <= 65535, RCHFSI_ERR_INVALID_ARG, "oz_gemm: grid too large");
   const CUtensorMap ma = slice_map(A, BM);
   const CUtensorMap mb = slice_map(B, BN);
-  const size_t smem = (size_t)ASTAGES * kABytes + 2 * (size_t)kBBytes + 1024;
-  RC_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = (size_t)ASTAGES * kABytes + 2 * (size_t)OzTile<BN>::kBBytes + 1024;
+  static const bool attr = [&] {
+    RC_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return true;
+  }();
+  (void)attr;
   OzArgs p;
   p.M = (int)M;
   p.N = (int)N;
@@ -449,7 +470,7 @@ void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B
     // tensor-core flops of the 28 slice products; bytes: the slices once and the FP64 output
     prof::Scope ps(s, RCHFSI_KERNEL_GEMM_F64_EMU, 2.0 * M * N * A.Kp * (S * (S + 1) / 2),
                    2.0 * S * (double)(M + N) * A.Kp + 8.0 * M * N);
-    oz_gemm_kernel<<<grid, kThreads, smem, s>>>(ma, mb, p);
+    oz_gemm_kernel<BN><<<grid, kThreads, smem, s>>>(ma, mb, p);
     RC_LAUNCH();
   }
   if (nsplit > 1) {
@@ -458,6 +479,29 @@ void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B
     oz_sum_kernel<<<blocks, 256, 0, s>>>(M, N, nsplit, p.C, C, ldc);
     RC_LAUNCH();
   }
+}
+
+}  // namespace
+
+void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
+             DevBuf<double>& ws, int* err) {
+  RC_CHECK(A.K == B.K && A.Kp == B.Kp, RCHFSI_ERR_INVALID_ARG, "oz_gemm: K mismatch");
+  const int64_t M = A.R, N = B.R;
+  RC_CHECK(M < (1LL << 31) && N < (1LL << 31), RCHFSI_ERR_INVALID_ARG, "oz_gemm: too large");
+  const int m_tiles = (int)((M + BM - 1) / BM);
+  const int nchunks = (int)(A.Kp / KC);
+  // tile width: 64 unless its padded columns or its worse wave fill cost more than the wider MMAs
+  // save (a 128 x 64 x 16 MMA takes 48 clocks, a 128 x 32 x 16 one 40: 1.67x the columns per clock)
+  double e32 = 0.0, e64 = 0.0;
+  const int t32 = m_tiles * (int)((N + 31) / 32), t64 = m_tiles * (int)((N + 63) / 64);
+  const int s32 = choose_split(t32, nchunks, num_sms, &e32);
+  const int s64 = choose_split(t64, nchunks, num_sms, &e64);
+  const double c32 = (double)((N + 31) / 32 * 32) / 1.0 / std::max(e32, 1e-3);
+  const double c64 = (double)((N + 63) / 64 * 64) / 1.67 / std::max(e64, 1e-3);
+  if (c64 < c32)
+    oz_gemm_launch<64>(s, num_sms, A, B, C, ldc, ws, err, s64);
+  else
+    oz_gemm_launch<32>(s, num_sms, A, B, C, ldc, ws, err, s32);
 }
 
 }  // namespace rchfsi
