@@ -49,7 +49,12 @@ def parse():
                     help="N x N projected eigensolver: cuSOLVER dsyevd, or this library's Jacobi or tridiagonal kernels")
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only: no comparisons, no end-to-end run, no CPU baseline (profiling runs)")
-    return ap.parse_args()
+    ap.add_argument("--fe-n", type=int, default=None,
+                    help="FE workload: n^3 cells instead of 16^3 (a smaller case for ncu captures)")
+    a = ap.parse_args()
+    if a.fe_n is not None:
+        FE["n"] = int(a.fe_n)
+    return a
 
 
 def workload_desc(kind, prec):
@@ -57,9 +62,10 @@ def workload_desc(kind, prec):
         return ("dense generalized A x = lambda B x, m=4000 (A: spectrum linspace(-1,10) + 0.05 gap after "
                 "index 50; B = S^1/2 (I + 0.1 G) S^1/2, diag(B)=S log-uniform[0.5,50]; D^-1 = diag(B)^-1), "
                 "nev=200, block=240, degree=30, %s filter products, FP64 Rayleigh-Ritz" % prec)
-    return ("FE generalized problem, periodic 16^3 Q4 cells (262,144 dofs), A = 0.5 K + V-mass (8 seeded "
+    n = FE["n"]
+    return ("FE generalized problem, periodic %d^3 Q4 cells (%s dofs), A = 0.5 K + V-mass (8 seeded "
             "wells), B = consistent mass, D^-1 = GLL-lumped inverse, nev=500, block=600, degree=25, "
-            "%s filter products, FP64 Rayleigh-Ritz" % prec)
+            "%s filter products, FP64 Rayleigh-Ritz" % (n, format((4 * n) ** 3, ","), prec))
 
 
 # Batched k-point workload: the structure of the 16-k-point configuration (Bloch problems on

@@ -65,7 +65,7 @@ __global__ void pack_slices_kernel(int64_t n_cells, int nc, const double* __rest
     for (int k = 0; k < kNCP; ++k) {
       long long f = (r < nc && k < nc) ? fixed56(row[k], ea) : 0;
       for (int s = 0; s < S; ++s) {
-        const long long t = next_digit(f, s);
+        const int t = (int)next_digit(f, s);
         *reinterpret_cast<__nv_bfloat16*>(base + (size_t)s * kASlice + sw_off2(r, k, kNCP)) =
             __float2bfloat16_rn((float)t);
       }
@@ -83,14 +83,39 @@ __global__ void colexp_kernel(int64_t m, int n, const double* __restrict__ X, in
 }
 
 // The 7 slice planes of X (row-major m x n): plane t holds the digits u_t, as BF16, row-major.
-__global__ void xslice_kernel(int64_t total, int n, const double* __restrict__ X, const int* __restrict__ cexp,
-                              __nv_bfloat16* __restrict__ planes) {
+// Thread (x, y): column pair 2 x of rows y, y + gridDim.y blockDim.y, ... (the column exponents are
+// loaded once; two columns per thread give 16-byte loads and 4-byte stores).  n even.
+__global__ void __launch_bounds__(256) xslice_kernel(int64_t m, int n, const double* __restrict__ X,
+                                                     const int* __restrict__ cexp,
+                                                     __nv_bfloat16* __restrict__ planes) {
+  const int j = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= n) return;
+  int e0 = cexp[j], e1 = cexp[j + 1];
+  if (e0 == -100000) e0 = 0;
+  if (e1 == -100000) e1 = 0;
+  const int64_t total = m * n;
+  for (int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; i < m; i += (int64_t)gridDim.y * blockDim.y) {
+    const int64_t e = i * n + j;
+    const double2 x = *reinterpret_cast<const double2*>(X + e);
+    long long f0 = fixed56(x.x, e0), f1 = fixed56(x.y, e1);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      // |digit| <= 256: converted through int (a 64-bit integer conversion uses the FP64 pipe)
+      const float d0 = (float)(int)next_digit(f0, t), d1 = (float)(int)next_digit(f1, t);
+      *reinterpret_cast<__nv_bfloat162*>(planes + (int64_t)t * total + e) = __floats2bfloat162_rn(d0, d1);
+    }
+  }
+}
+
+// Odd n: one column per thread.
+__global__ void xslice1_kernel(int64_t total, int n, const double* __restrict__ X, const int* __restrict__ cexp,
+                               __nv_bfloat16* __restrict__ planes) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int ex = cexp[e % n];
     if (ex == -100000) ex = 0;
     long long f = fixed56(X[e], ex);
 #pragma unroll
-    for (int t = 0; t < S; ++t) planes[(int64_t)t * total + e] = __float2bfloat16_rn((float)next_digit(f, t));
+    for (int t = 0; t < S; ++t) planes[(int64_t)t * total + e] = __float2bfloat16_rn((float)(int)next_digit(f, t));
   }
 }
 
@@ -140,17 +165,6 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
   lo += e;
 }
 
-// x (finite FP32, |x| in the normal range or 0) times 2^p as an FP64 value, by integer arithmetic.
-__device__ __forceinline__ double f32_scaled(float x, int p) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t e8 = (b >> 23) & 0xff;
-  if (e8 == 0) return 0.0;
-  const long long e = (long long)e8 - 127 + 1023 + p;
-  if (e <= 0 || e >= 2047) return ldexp((double)x, p);  // out of the normal range: rare, exact path
-  const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)e << 52) |
-                                  ((unsigned long long)(b & 0x7fffff) << 29);
-  return __longlong_as_double((long long)bits);
-}
 
 __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constant__ FeOzArgs p) {
   extern __shared__ uint8_t smem_raw[];
@@ -491,8 +505,15 @@ void fe_apply_f64_rows_tc(cudaStream_t s, const FeOp& op, bool useB, const doubl
   RC_LAUNCH();
   const int64_t total = m * n;
   __nv_bfloat16* planes = op.ozplanes.ensure((size_t)S * total);
-  xslice_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(total, n, X, cexp,
-                                                                                            planes);
+  if (n % 2 == 0) {
+    // 32 column pairs x 8 rows per block; enough row blocks for ~16 blocks per SM
+    const unsigned gx = cdiv(n / 2, 32);
+    const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 8), (int64_t)num_sms * 16 / gx + 1));
+    xslice_kernel<<<dim3(gx, gy), dim3(32, 8), 0, s>>>(m, n, X, cexp, planes);
+  } else {
+    xslice1_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(total, n, X, cexp,
+                                                                                               planes);
+  }
   RC_LAUNCH();
   if (!op.cplx) {
     launch_oz(s, num_sms, op, useB, planes, total, cexp, Y, n, false);

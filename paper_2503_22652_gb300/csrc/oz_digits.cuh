@@ -49,4 +49,16 @@ __device__ __forceinline__ long long next_digit(long long& f, int s) {
   return t;
 }
 
+// x (finite FP32, |x| in the normal range or 0) times 2^p as an FP64 value, by integer arithmetic.
+__device__ __forceinline__ double f32_scaled(float x, int p) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e8 = (b >> 23) & 0xff;
+  if (e8 == 0) return 0.0;
+  const long long e = (long long)e8 - 127 + 1023 + p;
+  if (e <= 0 || e >= 2047) return ldexp((double)x, p);  // out of the normal range: rare, exact path
+  const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)e << 52) |
+                                  ((unsigned long long)(b & 0x7fffff) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 }  // namespace rchfsi

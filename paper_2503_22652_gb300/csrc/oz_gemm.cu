@@ -115,7 +115,9 @@ __global__ void slice_kernel(int64_t R, int64_t Rp, int64_t K, int64_t Kp, const
         f0 -= t0 << sh;
         f1 -= t1 << sh;
       }
-      o2[(int64_t)s * Rp * Kp / 2] = __floats2bfloat162_rn((float)t0, (float)t1);
+      // digits fit in 32 bits (|t| <= 256): an int conversion stays off the FP64 pipe, which a
+      // 64-bit integer conversion occupies (a few DFMA per clock per SM on this GPU)
+      o2[(int64_t)s * Rp * Kp / 2] = __floats2bfloat162_rn((float)(int)t0, (float)(int)t1);
     }
   }
 }
@@ -309,7 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int u = 0; u < HC; ++u) {
           const int64_t jcol = (int64_t)n0 + h * HC + u;
           if (jcol < p.N) {
-            const double v = ldexp((double)hi[u] + (double)lo[u], ei + p.eb[jcol] - 16);
+            // (hi + lo) 2^(e_i + f_j - 16): exact conversions by exponent arithmetic and one FP64 add
+            const int pw = ei + p.eb[jcol] - 16;
+            const double v = f32_scaled(hi[u], pw) + f32_scaled(lo[u], pw);
             if (p.partial) p.C[((int64_t)split * p.N + jcol) * p.M + i] = v;
             else p.C[jcol * p.ldc + i] = v;
           }
