@@ -63,35 +63,50 @@ __global__ void __launch_bounds__(256) fe_cell_kernel(int nc, const int* __restr
   }
 }
 
+// Recurrence update of row-major m x n blocks, Rx = a W lam + b Ry + c Rx (W may be null).  Thread
+// (x, y) owns column j = 32 blockIdx.x + x and walks rows y, y + 8 gridDim.y, ...: its lam_j is read
+// and converted once (an FP64 conversion per element would occupy the FP64 pipe, and e % n costs a
+// 64-bit division), the warp's 32 columns are consecutive (coalesced).
 template <typename T>
-__global__ void recur_rows_kernel(int64_t total, int n, const T* __restrict__ Ry, T* __restrict__ Rx,
-                                  const T* __restrict__ W, const double* __restrict__ lam, T a, T b, T c) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) recur_rows_kernel(int64_t m, int n, const T* __restrict__ Ry, T* __restrict__ Rx,
+                                                         const T* __restrict__ W, const double* __restrict__ lam, T a,
+                                                         T b, T c) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  if (j >= n) return;
+  const T al = W ? a * (T)lam[j] : T(0);
+  for (int64_t i = blockIdx.y * 8 + threadIdx.y; i < m; i += (int64_t)gridDim.y * 8) {
+    const int64_t e = i * n + j;
     T v = b * Ry[e];
     if (c != T(0)) v += c * Rx[e];
-    if (W) v += a * W[e] * (T)lam[e % n];
+    if (W) v += al * W[e];
     Rx[e] = v;
   }
 }
 
 // Same update with (a, b, c) = coef[0..2] read on the device, so that a captured CUDA graph of the
 // filter loop stays valid when the Chebyshev coefficients change between outer iterations.
-__global__ void recur_rows_dev_kernel(int64_t total, int n, const float* __restrict__ Ry, float* __restrict__ Rx,
-                                      const float* __restrict__ W, const double* __restrict__ lam,
-                                      const double* __restrict__ coef) {
-  const float a = (float)coef[0], b = (float)coef[1], c = (float)coef[2];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) recur_rows_dev_kernel(int64_t m, int n, const float* __restrict__ Ry,
+                                                             float* __restrict__ Rx, const float* __restrict__ W,
+                                                             const double* __restrict__ lam,
+                                                             const double* __restrict__ coef) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  if (j >= n) return;
+  const float b = (float)coef[1], c = (float)coef[2];
+  const float al = W ? (float)(coef[0] * lam[j]) : 0.f;
+  for (int64_t i = blockIdx.y * 8 + threadIdx.y; i < m; i += (int64_t)gridDim.y * 8) {
+    const int64_t e = i * n + j;
     float v = b * Ry[e];
     if (c != 0.f) v += c * Rx[e];
-    if (W) v += a * W[e] * (float)lam[e % n];
+    if (W) v += al * W[e];
     Rx[e] = v;
   }
 }
 
-inline unsigned blocks_for(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
-  return (unsigned)(b < 1 ? 1 : b);
+// Grid of recur_rows kernels: 32-column strips, row blocks for ~16 CTAs per SM.
+inline dim3 recur_grid(int64_t m, int n) {
+  const unsigned gx = cdiv(n, 32);
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 8), (int64_t)152 * 16 / gx + 1));
+  return dim3(gx, (unsigned)std::min<int64_t>(gy, 65535));
 }
 
 template <typename T, int TN>
@@ -173,20 +188,20 @@ void fe_filter_product_f32(cudaStream_t s, FeOp& op, int precision, const float*
 
 void recur_terms_rows_f32(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
                           const double* lam, double a, double b, double c) {
-  recur_rows_kernel<float><<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, (float)a, (float)b,
-                                                             (float)c);
+  recur_rows_kernel<float><<<recur_grid(m, n), dim3(32, 8), 0, s>>>(m, n, Ry, Rx, W, lam, (float)a, (float)b,
+                                                                     (float)c);
   RC_LAUNCH();
 }
 
 void recur_terms_rows_f32_dev(cudaStream_t s, int64_t m, int n, const float* Ry, float* Rx, const float* W,
                               const double* lam, const double* coef) {
-  recur_rows_dev_kernel<<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, coef);
+  recur_rows_dev_kernel<<<recur_grid(m, n), dim3(32, 8), 0, s>>>(m, n, Ry, Rx, W, lam, coef);
   RC_LAUNCH();
 }
 
 void recur_terms_rows_f64(cudaStream_t s, int64_t m, int n, const double* Ry, double* Rx, const double* W,
                           const double* lam, double a, double b, double c) {
-  recur_rows_kernel<double><<<blocks_for(m * n), 256, 0, s>>>(m * n, n, Ry, Rx, W, lam, a, b, c);
+  recur_rows_kernel<double><<<recur_grid(m, n), dim3(32, 8), 0, s>>>(m, n, Ry, Rx, W, lam, a, b, c);
   RC_LAUNCH();
 }
 

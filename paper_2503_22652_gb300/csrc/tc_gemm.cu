@@ -46,12 +46,14 @@ __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float
 __device__ __forceinline__ void from_f(float& d, float v) { d = v; }
 __device__ __forceinline__ void from_f(__nv_bfloat16& d, float v) { d = __float2bfloat16_rn(v); }
 
+// lam_a = a lam[col] in FP32, formed once per column by the caller (an FP64 conversion per element
+// would occupy the FP64 pipe).
 template <typename T>
-__device__ __forceinline__ void apply_epi(const Epi<T>& e, int64_t row, int64_t col, float acc) {
+__device__ __forceinline__ void apply_epi(const Epi<T>& e, int64_t row, int64_t col, float acc, float lam_a) {
   const int64_t o = col * e.ld + row;
   float v = e.a * acc + e.b * to_f(e.Ry[o]);
   if (e.Rx) v += e.c * to_f(e.Rx[o]);
-  if (e.W) v += e.a * to_f(e.W[o]) * (float)e.lam[col];
+  if (e.W) v += to_f(e.W[o]) * lam_a;
   from_f(e.out[o], v);
 }
 
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int consumed;
+  __shared__ float s_lam[256];  // a lam_j of the tile's columns (BN <= 256)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, split = blockIdx.z;
@@ -93,6 +96,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::prefetch_tmap(&mapA);
     tc::prefetch_tmap(&mapB);
   }
+  if (ep.W && !ws)
+    for (int j = threadIdx.x; j < BN; j += blockDim.x) s_lam[j] = n0 + j < N ? (float)((double)ep.a * ep.lam[n0 + j]) : 0.f;
   if (warp == 1) {
     tc::tmem_alloc(&tmem_slot, tmem_cols);
     tc::tmem_relinquish();
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t col = (int64_t)n0 + c0 + t;
             if (col < N) {
               if (ws) ws[((int64_t)split * N + col) * M + row] = v[t];
-              else apply_epi(ep, row, col, v[t]);
+              else apply_epi(ep, row, col, v[t], ep.W ? s_lam[c0 + t] : 0.f);
             }
           }
         }
@@ -209,7 +214,7 @@ __global__ void splitk_reduce_kernel(int M, int N, int nsplit, const float* __re
     const int64_t col = e / M, row = e - col * M;
     float acc = 0.f;
     for (int s = 0; s < nsplit; ++s) acc += ws[(int64_t)s * total + e];
-    apply_epi(ep, row, col, acc);
+    apply_epi(ep, row, col, acc, ep.W ? ep.a * (float)ep.lam[col] : 0.f);
   }
 }
 

@@ -112,3 +112,23 @@ def test_rayleigh_ritz_syevd_parity():
     s = make_solver(case, 36, eig_mode="syevd")
     X, ev = s.rayleigh_ritz(case["X"])
     _check_rr(case["A"], case["B"], case["X"], X, ev)
+
+
+@pytest.mark.parametrize("N", [7, 40, 240])
+def test_rayleigh_ritz_tridiag_exact_diagonal(N):
+    """An exactly diagonal projected matrix (integer spectrum, Y = unit vectors): every Householder
+    step has nothing to annihilate (tau = 0), and Sturm minors of trial points that hit an integer
+    are exactly zero, the case the check-free Sturm count hands to the substituting recount.  The
+    Ritz values are the integers to a few ulps."""
+    m = N + 13
+    lam = np.arange(m, dtype=np.float64)[::-1] - 3.0          # ..., -2, -3, descending on the diagonal
+    A = np.diag(lam)
+    Y = np.eye(m)[:, :N]
+    s = Solver(m, nev=max(1, N // 2), block=N, eig_mode="tridiag")
+    s.set_dense(A)
+    X, ev = s.rayleigh_ritz(Y)
+    want = np.sort(lam[:N])
+    # the multisection interval closes to a few ulps around each integer
+    np.testing.assert_allclose(ev, want, rtol=0, atol=8 * np.finfo(float).eps * np.abs(lam).max())
+    np.testing.assert_allclose(np.abs(X.T @ X), np.eye(N), atol=1e-14)
+    np.testing.assert_allclose(X.T @ A @ X, np.diag(ev), atol=1e-13 * np.abs(lam).max())
