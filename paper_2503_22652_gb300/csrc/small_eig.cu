@@ -1111,6 +1111,36 @@ bool launch_resident(cudaStream_t s, void (*kc)(Args...), void (*kg)(Args...), i
   return true;
 }
 
+// Above this order the tridiagonalisation runs on a cooperative grid of one CTA per SM: its rank-2
+// updates, O(n^2) FP64 work per column, then outweigh the grid barrier's cost over the cluster's
+// (measured per Rayleigh-Ritz step: n = 240 cluster 4.10 ms / grid 4.52 ms, n = 600 18.8 / 16.3 ms;
+// a n^3 + b n fits put the crossover near 380).
+constexpr int kTriClusterMaxN = 384;
+
+// tridiag_smem_kernel on a cooperative grid of one CTA per SM when the owned columns fit in shared
+// memory; false otherwise.
+bool launch_tridiag_grid(cudaStream_t s, int n, int num_sms, const double* M, double* H, double* d, double* e,
+                         double* tau, double* xch, double* p) {
+  const int P = num_sms;
+  const size_t smem = resident_smem(n, P);
+  if (smem > SMEM_CAP) return false;
+  static const bool attr = [] {
+    RC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(tridiag_smem_kernel<false>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CAP));
+    return true;
+  }();
+  (void)attr;
+  int per_sm = 0;
+  RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_smem_kernel<false>, TRI_THREADS, smem));
+  if (per_sm < 1) return false;
+  int nn = n;
+  void* argv[] = {(void*)&nn, (void*)&M, (void*)&H, (void*)&d, (void*)&e, (void*)&tau, (void*)&xch, (void*)&p};
+  RC_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(tridiag_smem_kernel<false>), dim3(P),
+                                      dim3(TRI_THREADS), argv, smem, s));
+  RC_LAUNCH();
+  return true;
+}
+
 // One cluster of tridiag_dsmem_kernel when its CTAs hold the owned columns; false otherwise.
 bool launch_tridiag_dsmem(cudaStream_t s, int n, const double* M, double* H, double* d, double* e, double* tau) {
   static const int csz = cluster_size_for(reinterpret_cast<const void*>(tridiag_dsmem_kernel), TRI_THREADS, SMEM_CAP);
@@ -1166,7 +1196,8 @@ bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, Dev
   RC_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, s));
   RC_CUDA(cudaMemsetAsync(tau, 0, sizeof(double) * n, s));
   // 1. Q^T M Q = T
-  if (!launch_tridiag_dsmem(s, n, M, H, d, e, tau) &&
+  if (!(n <= kTriClusterMaxN ? launch_tridiag_dsmem(s, n, M, H, d, e, tau)
+                             : launch_tridiag_grid(s, n, num_sms, M, H, d, e, tau, xch, p)) &&
       !launch_resident(s, tridiag_smem_kernel<true>, tridiag_smem_kernel<false>, n, num_sms, n, (const double*)M, H,
                        d, e, tau, xch, p))
     launch_multi(s, tridiag_kernel<true>, tridiag_kernel<false>, n, num_sms, n, M, H, d, e, tau, p);

@@ -30,10 +30,10 @@ def _check_rr(A, Bm, Y, X, ev, rtol=1e-11, vec_tol=1e-9):
     return Xr, evr
 
 
-# (m, N): N = 1, 2, 3 edge cases; 36 and 240 on the thread-block-cluster path; 1100 on the
-# cooperative-grid path (order above 1024)
+# (m, N): N = 1, 2, 3 edge cases; 36 and 240 on the thread-block-cluster path; 480 and 1100 on the
+# cooperative-grid path
 @pytest.mark.parametrize("m,N,gen", [(50, 1, False), (60, 2, True), (70, 3, False), (280, 36, True),
-                                     (900, 240, True), (1300, 1100, False)])
+                                     (900, 240, True), (700, 480, True), (1300, 1100, False)])
 def test_rayleigh_ritz_tridiag_parity(m, N, gen):
     case = dense_case(m=m, N=N, generalized=gen)
     Bm = case["B"] if gen else np.eye(m)
