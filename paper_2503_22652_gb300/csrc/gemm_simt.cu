@@ -141,8 +141,27 @@ __global__ void __launch_bounds__(256) gemv_kernel(int64_t M, int N, int64_t K, 
   const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= M) return;
-  T acc[4] = {T(0), T(0), T(0), T(0)};
   const T* arow = A + i * lda;
+  if (N == 1) {
+    // one column: four independent partial sums (no FMA on columns that do not exist; on this GPU
+    // a warp-wide FP64 instruction holds the FP64 pipe whether or not its result is used)
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int64_t k = lane;
+    for (; k + 96 < K; k += 128) {
+      const int64_t s1 = BKC ? 32 : 32 * ldb;
+      const T* b = BKC ? B + k : B + k * ldb;
+      a0 = fma(arow[k], b[0], a0);
+      a1 = fma(arow[k + 32], b[s1], a1);
+      a2 = fma(arow[k + 64], b[2 * s1], a2);
+      a3 = fma(arow[k + 96], b[3 * s1], a3);
+    }
+    for (; k < K; k += 32) a0 = fma(arow[k], BKC ? B[k] : B[k * ldb], a0);
+    T v = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) epi(i, 0, v);
+    return;
+  }
+  T acc[4] = {T(0), T(0), T(0), T(0)};
   for (int64_t k = lane; k < K; k += 32) {
     const T a = arow[k];
 #pragma unroll
