@@ -41,15 +41,19 @@ struct OzTile {
 };
 
 // ---------------------------------------------------------------- slicing
-// Row exponents, K-contiguous rows: one warp per row.
+// Row exponents, K-contiguous rows: one warp per (row, K slice), the K range split over
+// blockIdx.y so that a few hundred rows still fill the GPU; slices meet in ex by atomicMax (ex
+// preset to INT_MIN), rowexp_fix maps rows without a nonzero element to 0.
 __global__ void rowexp_kcontig(int64_t R, int64_t K, const double* __restrict__ X, int64_t rs, int* ex) {
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (r >= R) return;
+  const int64_t kb = (K + gridDim.y - 1) / gridDim.y, k0 = (int64_t)blockIdx.y * kb;
+  const int64_t k1 = k0 + kb < K ? k0 + kb : K;
   int e = -100000;
-  for (int64_t k = lane; k < K; k += 32) e = max(e, exp_of(X[r * rs + k]));
+  for (int64_t k = k0 + lane; k < k1; k += 32) e = max(e, exp_of(X[r * rs + k]));
   for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-  if (lane == 0) ex[r] = (e == -100000) ? 0 : e;
+  if (lane == 0) atomicMax(ex + r, e);
 }
 
 // Row exponents, rows contiguous across threads (element (r, k) at X[r + k * ks]): 32 rows per
@@ -394,7 +398,14 @@ void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs,
   prof::Scope ps(s, RCHFSI_KERNEL_RR_AUX, 0.0, 8.0 * R * K + 2.0 * S * op.Rp * op.Kp);
   if (op.Rp > R) RC_CUDA(cudaMemsetAsync(op.sl.p, 0, sizeof(__nv_bfloat16) * S * op.Rp * op.Kp, s));
   if (ks == 1) {
-    rowexp_kcontig<<<cdiv(R, 8), 256, 0, s>>>(R, K, X, rs, op.ex.p);
+    // K slices of >= 256 elements, enough (row, slice) warps for ~16 per SM
+    const unsigned rb = cdiv(R, 8);
+    const unsigned kb = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(cdiv(K, 256), (int64_t)(sm_count() * 16 * 8) / std::max<int64_t>(R, 1)));
+    RC_CUDA(cudaMemsetAsync(op.ex.p, 0x80, sizeof(int) * R, s));  // 0x80808080: below every exponent
+    rowexp_kcontig<<<dim3(rb, kb), 256, 0, s>>>(R, K, X, rs, op.ex.p);
+    RC_LAUNCH();
+    rowexp_fix<<<cdiv(R, 256), 256, 0, s>>>(R, op.ex.p);
   } else {
     // enough blocks to fill the GPU a few times over, each warp walking at least 8 k
     const unsigned rb = cdiv(R, 32);
