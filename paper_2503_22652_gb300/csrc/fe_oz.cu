@@ -15,8 +15,9 @@
 //   warps 0-7  gather: thread (k, h) copies its dof k's row, columns h*BN/2.., of the 7 X slice
 //              planes (sliced once per product by xslice_kernel) into the K-major 128-byte-swizzled
 //              shared images X_c^(t);
-//   warp 8     MMA issuer (one lane): for each A slice s (streamed through a 2-deep ring) the
-//              products with X_c^(t), t <= 6 - s, into the TMEM accumulator of level s + t;
+//   warp 8     MMA issuer (the whole warp over an unrolled sequence, one elected lane issuing):
+//              for each A slice s (streamed through a 2-deep ring) the products with X_c^(t),
+//              t <= 6 - s, into the TMEM accumulator of level s + t;
 //   warps 9-16 epilogue (two per TMEM lane quarter, alternate 16 columns): tcgen05.ld of the 7
 //              levels, float-float fold, exact conversion and exponent scaling by integer
 //              arithmetic, one FP64 add, FP64 atomic scatter-add;

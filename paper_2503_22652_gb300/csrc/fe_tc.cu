@@ -9,8 +9,9 @@
 //              loads in flight), scales by D^-1, rounds to the operand type and writes it transposed
 //              into the K-major 128-byte-swizzled shared-memory image of X_c (two stages), then
 //              fence.proxy.async + mbarrier arrive;
-//   warp 8     MMA issuer (one lane): tcgen05.mma kind::tf32 (K = 8) or kind::f16 (BF16, K = 16)
-//              into one of two TMEM accumulators, tcgen05.commit to release stages / buffers;
+//   warp 8     MMA issuer (the whole warp, one elected lane issuing): tcgen05.mma kind::tf32
+//              (K = 8) or kind::f16 (BF16, K = 16) into one of two TMEM accumulators,
+//              tcgen05.commit to release stages / buffers;
 //   warps 9-12 epilogue: tcgen05.ld of the accumulator rows (thread = cell-local dof), scaling, and
 //              vectorised float4 atomic scatter-add into R_X (dofs shared by neighbouring cells get
 //              one add per cell);

@@ -1,13 +1,17 @@
 // FP64-accurate products from BF16 tensor-core slices (see oz_gemm.cuh for the scheme).
 //
-// oz_gemm_kernel: one CTA per 128 x 32 output tile and K range.  Warp 0 (one lane) streams, per
-// 64-wide K chunk, the 7 B slices of the tile (one 28 KB stage, two stages) and the 7 A slices
-// (16 KB each, a 6-deep ring) with TMA; warp 1 (one lane) issues, for each A slice s, the products
-// with B slices t <= 6 - s (4 x tcgen05.mma kind::f16, K = 16) into the TMEM accumulator of level
-// s + t (7 levels x 32 columns, two buffers = 448 columns), accumulating GROUP chunks per buffer;
-// warps 4-11 (two per TMEM lane quarter, 16 columns each) drain a finished group: tcgen05.ld of the
-// 7 levels, exact scaling by 2^-8L and TwoSum into per-output float-float accumulators.  The final value (hi + lo) 2^(e_i + f_j - 16) is
-// stored in FP64 (or, with split-K, written as a partial and summed by a second kernel).
+// oz_gemm_kernel<BN>: one CTA per 128 x BN output tile (BN = 32 or 64) and K range.  Warp 0 (one
+// lane) streams, per 64-wide K chunk, the 7 B slices of the tile (one 28 / 56 KB stage, two stages)
+// and the 7 A slices (16 KB each, a 6-deep ring) with TMA; warp 1 (the whole warp, one elected lane
+// issuing) runs, for each A slice s, the products with B slices t <= 6 - s (4 x tcgen05.mma
+// kind::f16, K = 16) into the TMEM accumulator of level s + t (7 levels x BN columns: two buffers
+// for BN = 32, one for BN = 64, 448 columns either way), accumulating GROUP chunks per buffer;
+// warps 4-11 (two per TMEM lane quarter, BN / 2 columns each) drain a finished group: tcgen05.ld of
+// the 7 levels, exact scaling by 2^-8L and TwoSum into per-output float-float accumulators.  The
+// final value (hi + lo) 2^(e_i + f_j - 16), formed by exponent arithmetic, is stored in FP64 (or,
+// with split-K, written as a partial and summed by a second kernel).  The host picks BN and the
+// split from the padded columns, the MMA rate (48 clocks per 128 x 64 x 16 MMA, 40 per 128 x 32 x
+// 16) and the wave fill.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
