@@ -310,6 +310,16 @@ def run_psweep(args, rank, world, local_rank):
             "best": best, "sweep": r}
 
 
+def max_over_ranks(x, device):
+    """The largest of every rank's x (the job's time is its slowest rank's); collective over the
+    default process group (NCCL on GPUs, gloo on host tensors)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_problem(kind):
     if kind == "dense":
         c = wl.dense_config2(m=DENSE["m"])
@@ -617,9 +627,7 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.stop()
     total = sum(times)
     if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+        total = max_over_ranks(total, dev)
     ms = total / args.steps
     st_last = st
     pk = peaks()
