@@ -299,7 +299,8 @@ typedef enum {
                                       the tensor-core flops (28 slice products) */
   RCHFSI_KERNEL_SMALL_DENSE = 7,   /* N x N steps of Rayleigh-Ritz: Cholesky, triangular solves,
                                       symmetrisation */
-  RCHFSI_KERNEL_EIG = 8,           /* projected N x N eigensolver (syevd library call or Jacobi kernel) */
+  RCHFSI_KERNEL_EIG = 8,           /* projected N x N eigensolver (this library's tridiagonal or Jacobi
+                                      kernels, or the cuSOLVER dsyevd call of RCHFSI_EIG_SYEVD) */
   RCHFSI_KERNEL_RR_AUX = 9,        /* m x N passes of Rayleigh-Ritz: column norms and scaling, BF16
                                       slicing of the emulated GEMM operands */
   RCHFSI_KERNEL_CLASSES = 10
@@ -329,9 +330,11 @@ int rchfsi_profile_read(struct rchfsi_ctx* h, int kernel_class, double* total_ms
  *   out = a * (A Ry) + b * Ry + c * Rx + a * W diag(lambda_y)
  *   A        m x m FP32, row-major, row pitch lda (the operator A D^-1, values read as TF32)
  *   Ry, Rx, W, out   m x n FP32, column-major, leading dimension ldr; Rx and W may be NULL (their
- *            terms are dropped); out may alias Rx but not Ry or W
+ *            terms are dropped); out may be the same array as Rx, but must not overlap Ry, W or
+ *            only part of Rx (checked on the byte ranges; INVALID_ARG otherwise)
  *   lambda_y n doubles
- * lda and ldr must be >= m and multiples of 4; all arrays are device memory of the current device;
+ * lda and ldr must be >= m and multiples of 4; all arrays are device memory of the current device
+ * (or managed memory; device memory of another GPU is refused with INVALID_ARG);
  * cuda_stream is the stream to run on (NULL = legacy default stream).  Returns after the step has
  * completed (the stream is synchronised).
  * Scratch: the split-K partial sums live in one file-scope __device__ array of

@@ -23,6 +23,9 @@ ERR_CUDA = -8
 ERR_NO_OPERATOR = -9
 ERR_UNSUPPORTED = -10
 
+# RCHFSI_STATIC_SCRATCH_FLOATS of include/rchfsi.h
+STATIC_SCRATCH_FLOATS = 4 * 1024 * 1024
+
 FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
 METHOD_RCHFSI, METHOD_CHFSI = 0, 1

@@ -6,7 +6,9 @@
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <thread>
+#include <tuple>
 
 #include "solver.cuh"
 
@@ -27,6 +29,18 @@ Profiler*& current() {
 int64_t& launch_counter() {
   static int64_t n = 0;
   return n;
+}
+
+void set_smem_limit(const void* kernel, int bytes) {
+  int dev = 0;
+  RC_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(kernel, dev, bytes);
+  if (done.count(key)) return;
+  RC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert(key);
 }
 }  // namespace rchfsi
 

@@ -34,6 +34,11 @@ struct Error : std::runtime_error {
 // Count of this library's kernel launches (read through rchfsi_profile_read).
 int64_t& launch_counter();
 
+// Raise a kernel's dynamic shared-memory limit on the current device to `bytes`.  The attribute is
+// per function and per device and shared by every host thread: this sets it once per (kernel,
+// device, size) under a lock, so concurrent callers on any device never launch before it is set.
+void set_smem_limit(const void* kernel, int bytes);
+
 #define RC_LAUNCH()                                   \
   do {                                                \
     RC_CUDA(cudaGetLastError());                      \

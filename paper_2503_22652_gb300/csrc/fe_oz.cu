@@ -458,11 +458,7 @@ void ensure_slices(cudaStream_t s, const FeOp& op, bool useB) {
 
 void launch_oz(cudaStream_t s, int num_sms, const FeOp& op, bool useB, const __nv_bfloat16* planes,
                int64_t plane_stride, const int* cexp, double* Y, int n, bool neg) {
-  static const bool attr_set = [] {
-    RC_CUDA(cudaFuncSetAttribute(fe_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024));
-    return true;
-  }();
-  (void)attr_set;
+  set_smem_limit(reinterpret_cast<const void*>(fe_oz_kernel), 232448 - 1024);
   ensure_slices(s, op, useB);
   const bool shared = useB && op.B_shared;
   FeOzArgs a{};

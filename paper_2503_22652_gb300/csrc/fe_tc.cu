@@ -433,14 +433,8 @@ void fe_tc_batch(cudaStream_t s, int precision, const FeTcPart* parts, int npart
   const size_t smem = 2 * per_cell + 2 * (size_t)b.maxBN * kNCP * ES + 1024;
   RC_CHECK(smem <= 232448 - 1024, RCHFSI_ERR_INVALID_ARG, "FE tensor path: shared memory plan too large");
   auto kern = bf ? fe_tc_kernel<true> : fe_tc_kernel<false>;
-  // the attribute is per function, shared by every host thread: set it once, to the largest plan
-  // (a per-launch value would race with a concurrent launch of a wider plan)
-  static const bool attr_set = [] {
-    for (auto k : {fe_tc_kernel<true>, fe_tc_kernel<false>})
-      RC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 1024));
-    return true;
-  }();
-  (void)attr_set;
+  // one limit for every plan (a per-launch value would race with a concurrent launch of a wider plan)
+  set_smem_limit(reinterpret_cast<const void*>(kern), 232448 - 1024);
   const unsigned grid = (unsigned)std::min<int64_t>(b.total_cells, (int64_t)num_sms);
   prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, flops, bytes);
   kern<<<grid, kThreads, smem, s>>>(b);

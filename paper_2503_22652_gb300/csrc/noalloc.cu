@@ -52,14 +52,27 @@ DeviceAddrs device_addrs() {
   return d;
 }
 
-bool on_device(const void* p) {
+// True for memory the current device `dev` can use as a kernel argument: its own device memory, or
+// managed memory.  Device memory of another GPU is refused (its address would reach the TMA maps).
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
+
+// Byte range [lo, hi) covered by an m x n column-major FP32 block of leading dimension ld.
+struct Span {
+  uintptr_t lo, hi;
+};
+Span block_span(const float* p, int64_t m, int64_t n, int64_t ld) {
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(p);
+  return {lo, lo + (uintptr_t)(((n - 1) * ld + m) * (int64_t)sizeof(float))};
+}
+bool overlap(const Span& a, const Span& b) { return a.lo < b.hi && b.lo < a.hi; }
 
 }  // namespace
 }  // namespace rchfsi
@@ -74,10 +87,18 @@ extern "C" int rchfsi_filter_step_tf32_static(const float* A, int64_t lda, const
     RC_CHECK(lda >= m && ldr >= m && (lda * 4) % 16 == 0 && (ldr * 4) % 16 == 0, RCHFSI_ERR_INVALID_ARG,
              "lda and ldr must be >= m and multiples of 4 (16-byte rows)");
     RC_CHECK(A && Ry && out && lambda_y, RCHFSI_ERR_INVALID_ARG, "A, Ry, lambda_y and out are required");
-    RC_CHECK(on_device(A) && on_device(Ry) && on_device(out) && (!Rx || on_device(Rx)) && (!W || on_device(W)) &&
-                 on_device(lambda_y),
-             RCHFSI_ERR_INVALID_ARG, "every array must be device memory");
-    RC_CHECK(out != Ry && out != W, RCHFSI_ERR_INVALID_ARG, "out may alias Rx only");
+    int dev = 0;
+    RC_CUDA(cudaGetDevice(&dev));
+    RC_CHECK(on_device(A, dev) && on_device(Ry, dev) && on_device(out, dev) && (!Rx || on_device(Rx, dev)) &&
+                 (!W || on_device(W, dev)) && on_device(lambda_y, dev),
+             RCHFSI_ERR_INVALID_ARG, "every array must be device (or managed) memory of the current device");
+    // out is written while Ry and W are still read by other threads: it may coincide with Rx (each
+    // element is read before it is written by the same thread) but must not overlap Ry, W or part
+    // of Rx
+    const Span so = block_span(out, m, n, ldr);
+    RC_CHECK(!overlap(so, block_span(Ry, m, n, ldr)) && (!W || !overlap(so, block_span(W, m, n, ldr))) &&
+                 (!Rx || Rx == out || !overlap(so, block_span(Rx, m, n, ldr))),
+             RCHFSI_ERR_INVALID_ARG, "out may coincide with Rx but must not overlap Ry, W or part of Rx");
     const DeviceAddrs d = device_addrs();
     const size_t need = tc_gemm_tf32_split_floats(d.sms, m, n, m);
     RC_CHECK(need <= kScratchFloats, RCHFSI_ERR_INVALID_ARG,

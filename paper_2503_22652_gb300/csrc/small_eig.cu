@@ -1206,12 +1206,7 @@ bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, Dev
   RC_LAUNCH();
   // 3. eigenvectors of T (into V2)
   RC_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
-  static bool attr_set = false;
-  if (!attr_set) {
-    RC_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(inviter_kernel),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CAP));
-    attr_set = true;
-  }
+  set_smem_limit(reinterpret_cast<const void*>(inviter_kernel), (int)SMEM_CAP);
   inviter_kernel<<<n, 32, inviter_smem(n), s>>>(n, d, e, evals, tnorm, V2, INV_MAX_CLUSTER, d_flag);
   RC_LAUNCH();
   int flag = 0;

@@ -286,11 +286,7 @@ void run(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64_t K, const T* 
   const Plan p = make_plan(num_sms, M, N, K, BK);
   const CUtensorMap ma = make_map(A, bf, K, M, lda, kBM);
   const CUtensorMap mb = make_map(B, bf, K, N, ldb, p.BN);
-  static bool attr_set = false;
-  if (!attr_set) {
-    RC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 4096));
-    attr_set = true;
-  }
+  set_smem_limit(reinterpret_cast<const void*>(tc_gemm_kernel<T>), 232448 - 4096);
   float* ws = nullptr;
   if (p.nsplit > 1) ws = split.ensure((size_t)p.nsplit * M * N);
   dim3 grid(p.m_tiles, p.n_tiles, p.nsplit);
@@ -347,7 +343,7 @@ void tc_gemm_tf32_recur_ws(cudaStream_t s, int num_sms, int64_t M, int64_t N, in
                std::to_string(ws_floats));
   const CUtensorMap ma = make_map(A, false, K, M, lda, kBM);
   const CUtensorMap mb = make_map(B, false, K, N, ldb, p.BN);
-  RC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448 - 4096));
+  set_smem_limit(reinterpret_cast<const void*>(tc_gemm_kernel<float>), 232448 - 4096);
   Epi<float> ep{r.a, r.b, r.c, r.Ry, r.Rx, r.W, r.lam, r.out, ldo};
   float* w = p.nsplit > 1 ? ws : nullptr;
   dim3 grid(p.m_tiles, p.n_tiles, p.nsplit);

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
+from oracle.chebyshev import affine, recurrence_coefficients
 from oracle.filters import lambda_p
 from gpu_helpers import ensure_built
 
@@ -34,19 +35,9 @@ def _tf32_rna(t):
 
 
 def _scalars(lmin, lT, lmax, p):
-    """e, c, sigma_1 and the (a_k, b_k, c_k) of the degree loop, with the library's operation order."""
-    e = 0.5 * (lmax - lT)
-    cc = 0.5 * (lmax + lT)
-    s1 = e / (lmin - cc)
-    gamma = 2.0 / s1
-    sigma = s1
-    co = []
-    for _ in range(2, p + 1):
-        s2 = 1.0 / (gamma - sigma)
-        a = 2.0 * s2 / e
-        co.append((a, -a * cc, -sigma * s2))
-        sigma = s2
-    return e, cc, s1, co
+    """e, c, sigma_1 and the (a_k, b_k, c_k) of the degree loop, from the oracle's definitions."""
+    e, cc, s1 = affine(lmin, lT, lmax)
+    return e, cc, s1, recurrence_coefficients(lmin, lT, lmax, p)
 
 
 def _lambda_rows(lam, e, cc, s1, co):
@@ -123,10 +114,22 @@ def test_static_scratch_step_matches_filter_two_calls(setup):
         assert err <= TF32_TOL, (deg, err)
 
 
+def _last_error(lib):
+    buf = C.create_string_buffer(512)
+    lib.rchfsi_last_error(None, buf, 512)
+    return buf.value
+
+
 def test_static_scratch_rejects_oversized_problem(setup):
     S = setup
     torch, lib = S["torch"], S["lib"]
-    m, N = 2000, 256   # split-K partials of this shape exceed the static array
+    # 65 row tiles of 128 and one 256-wide column tile: on any GPU with >= 130 SMs the product is
+    # split over K at least twice, and two splits of 8200 x 256 partials already exceed the array
+    m, N = 8200, 256
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if sms // ((m + 127) // 128) < 2:
+        pytest.skip("this GPU would not split the product over K")
+    assert 2 * m * N > S["_lib"].STATIC_SCRATCH_FLOATS
     A = torch.zeros(m, m, dtype=torch.float32, device="cuda")
     R = torch.zeros(N, m, dtype=torch.float32, device="cuda")
     out = torch.zeros(N, m, dtype=torch.float32, device="cuda")
@@ -134,6 +137,28 @@ def test_static_scratch_rejects_oversized_problem(setup):
     rc = lib.rchfsi_filter_step_tf32_static(A.data_ptr(), m, R.data_ptr(), None, None, lam.data_ptr(), 1.0, 0.0,
                                             0.0, m, N, m, out.data_ptr(), None)
     assert rc == S["_lib"].ERR_INVALID_ARG
-    buf = C.create_string_buffer(512)
-    lib.rchfsi_last_error(None, buf, 512)
-    assert b"static limit" in buf.value
+    assert b"static limit" in _last_error(lib)
+
+
+def test_static_scratch_rejects_partial_overlap(setup):
+    """out may be Rx itself, but an out that overlaps part of Ry, W or Rx is refused before any
+    kernel runs."""
+    S = setup
+    torch, lib = S["torch"], S["lib"]
+    m, N = 256, 32
+    A = torch.zeros(m, m, dtype=torch.float32, device="cuda")
+    big = torch.zeros(4 * N * m, dtype=torch.float32, device="cuda")
+    Ry, W, Rx = big[:N * m], big[N * m:2 * N * m], big[2 * N * m:3 * N * m]
+    lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+
+    def call(out_ptr, rx_ptr):
+        return lib.rchfsi_filter_step_tf32_static(A.data_ptr(), m, Ry.data_ptr(), rx_ptr, W.data_ptr(),
+                                                  lam.data_ptr(), 1.0, 0.0, 0.0, m, N, m, out_ptr, None)
+
+    shifted = big.data_ptr() + 4 * 4   # 4 floats into Ry: overlaps Ry
+    assert call(shifted, None) == S["_lib"].ERR_INVALID_ARG
+    assert b"overlap" in _last_error(lib)
+    assert call(W.data_ptr() + 64, None) == S["_lib"].ERR_INVALID_ARG   # overlaps W
+    assert call(Rx.data_ptr() + 16, Rx.data_ptr()) == S["_lib"].ERR_INVALID_ARG   # part of Rx
+    assert call(Rx.data_ptr(), Rx.data_ptr()) == S["_lib"].OK   # out is Rx itself: allowed
+    torch.cuda.synchronize()
