@@ -307,13 +307,15 @@ typedef enum {
 } rchfsi_kernel_class;
 
 /* enable = 1: start timing every instrumented launch of this handle with CUDA events on the
- * launching stream (previous records are cleared); enable = 0: stop and clear. */
+ * launching stream (previous records are cleared); enable = 0: stop and clear.  Either value
+ * restarts the launch count read with kernel_class = RCHFSI_KERNEL_CLASSES, so enable = 0 counts
+ * launches without adding any event to the stream. */
 int rchfsi_profile(struct rchfsi_ctx* h, int enable);
 
 /* Totals for one kernel class since rchfsi_profile(h, 1): device time (ms), number of launches,
  * and the algorithmic flops and bytes of those launches (each may be NULL).  Synchronises the
  * handle's stream.  kernel_class = RCHFSI_KERNEL_CLASSES returns in *launches the number of all
- * kernel launches of this library (any handle, any thread) since rchfsi_profile(h, 1). */
+ * kernel launches of this library (any handle, any thread) since the last rchfsi_profile(h, .). */
 int rchfsi_profile_read(struct rchfsi_ctx* h, int kernel_class, double* total_ms, int64_t* launches,
                         double* flops, double* bytes);
 

@@ -1020,7 +1020,7 @@ int rchfsi_profile_read(rchfsi_ctx* h, int cls, double* total_ms, int64_t* launc
     RC_CHECK(cls >= 0 && cls <= RCHFSI_KERNEL_CLASSES, RCHFSI_ERR_INVALID_ARG, "bad kernel class");
     if (h->s) RC_CUDA(cudaStreamSynchronize(h->s));
     if (cls == RCHFSI_KERNEL_CLASSES) {
-      // all kernel launches of this library (every thread) since rchfsi_profile(h, 1)
+      // all kernel launches of this library (every thread) since the last rchfsi_profile(h, .)
       if (launches) *launches = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED) - h->prof.launch_base;
       if (total_ms) *total_ms = 0.0;
       if (flops) *flops = 0.0;

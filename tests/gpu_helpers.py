@@ -86,3 +86,15 @@ def round_mantissa(x, bits, mode="nearest"):
     else:
         q = np.round(m * scale)
     return np.ldexp(q / scale, e)
+
+
+def lowp_reference(case, p, bits_op, bits_r, r_mode, lmin, lT, lmax):
+    """Oracle Algorithm 3 whose product consumes the operator rounded to `bits_op` mantissa bits and
+    R_Y rounded to `bits_r` bits (the inputs the tensor cores / FP32 units see)."""
+    _, Dinv, _ = oracle_ops(case)
+    d = case["Dinv"]
+    F = case["A"] if case["A_filter"] is None else case["A_filter"]
+    Ad = F * d[None, :] if d is not None else F
+    Ar = round_mantissa(Ad, bits_op)
+    ADr = lambda R: Ar @ round_mantissa(round_mantissa(R, 23), bits_r, r_mode)  # noqa: E731
+    return filters.rchfsi_filter(ADr, Dinv, case["X"], case["L"], case["W"], lmin, lT, lmax, p)

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import filters
-from gpu_helpers import ensure_built, dense_case, oracle_ops, make_solver, relfro, round_mantissa
+from gpu_helpers import ensure_built, dense_case, oracle_ops, make_solver, relfro, lowp_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -45,18 +45,6 @@ def test_chfsi_filter_fp64_parity(cfg):
     assert relfro(got, ref) <= FP64_TOL
 
 
-def _lowp_reference(case, p, bits_op, bits_r, r_mode, lmin, lT, lmax):
-    """Oracle Algorithm 3 whose product consumes the operator rounded to `bits_op` mantissa bits and
-    R_Y rounded to `bits_r` bits (the inputs the tensor cores / FP32 units see)."""
-    AD, Dinv, _ = oracle_ops(case)
-    d = case["Dinv"]
-    F = case["A"] if case["A_filter"] is None else case["A_filter"]
-    Ad = F * d[None, :] if d is not None else F
-    Ar = round_mantissa(Ad, bits_op)
-    ADr = lambda R: Ar @ round_mantissa(round_mantissa(R, 23), bits_r, r_mode)  # noqa: E731
-    return filters.rchfsi_filter(ADr, Dinv, case["X"], case["L"], case["W"], lmin, lT, lmax, p)
-
-
 # Tolerances for the reduced-precision filters, relative to ||Y_p - X Lambda_p|| (the part of Y_p
 # that the low-precision recurrence produces).  The oracle sees the same rounded operator and the
 # same rounding of R_Y as the GPU; what remains is FP32 accumulation (u = 6e-8 times sqrt(K)
@@ -72,7 +60,7 @@ def test_rchfsi_filter_lowp_parity(prec, cfg):
     case = dense_case(**cfg)
     bits_op, bits_r, mode, tol = LOWP[prec]
     (lmin, lT, lmax), p = case["bounds"], 10
-    ref = _lowp_reference(case, p, bits_op, bits_r, mode, lmin, lT, lmax)
+    ref = lowp_reference(case, p, bits_op, bits_r, mode, lmin, lT, lmax)
     s = make_solver(case, cfg["N"], precision=prec)
     got = s.filter(case["X"], case["L"], case["W"], lmin, lT, lmax, p)
     from oracle.filters import lambda_p
