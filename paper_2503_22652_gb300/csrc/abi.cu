@@ -372,6 +372,22 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
   RC_CUDA(cudaStreamSynchronize(c.s));
   for (size_t i = 0; i < nd; ++i)
     RC_CHECK(hd[i] >= 0 && hd[i] < mc, RCHFSI_ERR_INVALID_ARG, "cell_dofs entry out of [0, m)");
+  // owner of each dof: the first cell (in cell order) that contains it
+  {
+    std::vector<uint32_t> own((size_t)f.n_cells * 4, 0u);
+    std::vector<uint8_t> seen((size_t)mc, 0);
+    for (int64_t cl = 0; cl < f.n_cells; ++cl)
+      for (int k = 0; k < f.nc; ++k) {
+        const int d = hd[(size_t)cl * f.nc + k];
+        if (!seen[d]) {
+          seen[d] = 1;
+          own[(size_t)cl * 4 + (k >> 5)] |= 1u << (k & 31);
+        }
+      }
+    RC_CUDA(cudaMemcpyAsync(f.own.ensure(own.size()), own.data(), own.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+  }
   const size_t nb = f.B_shared ? (size_t)f.nc * f.nc : na;
   to_device(c, op->B_cells, f.B64.ensure(nb), nb);
   f.err = c.w.info.p + 2;
@@ -393,6 +409,7 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
     to_device(c, op->A_cells, tmp.ensure(2 * na), 2 * na);
     cplx_deinterleave(c.s, na, tmp.p, f.A64.ensure(na), g.A64.ensure(na));
     RC_CUDA(cudaMemcpyAsync(g.dofs.ensure(nd), dofs, nd * sizeof(int), cudaMemcpyDeviceToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(g.own.ensure(f.own.n), f.own.p, f.own.bytes(), cudaMemcpyDeviceToDevice, c.s));
     // D^-1 of the embedding: [D^-1; D^-1]
     double* dv = f.Dinv.ensure(2 * mc);
     to_device(c, op->Dinv, dv, mc);

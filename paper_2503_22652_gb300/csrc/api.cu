@@ -15,6 +15,7 @@
 #include "solver.cuh"
 #include "tc_gemm.cuh"
 #include "fe_tc.cuh"
+#include "fe_step.cuh"
 
 #include <map>
 #include <tuple>
@@ -181,6 +182,28 @@ static void lambda_table(const double* lam, int N, double e, double cc, double s
       tab[(size_t)(k + 2) * N + j] = ly;
     }
   }
+}
+
+// Scales s_k of the iterates S_k = s_k R_k of the fused FE step (s_1 = s_2 = 1, s_k = s_{k-2} / c_k,
+// so that S_{k-2} enters step k with coefficient 1); false when one leaves [2^-60, 2^60] (the
+// unfused step is used then).
+static bool fused_scales(const std::vector<Coef>& co, std::vector<double>& sc) {
+  const int p = (int)co.size() + 1;
+  sc.assign((size_t)p + 1, 1.0);
+  for (int k = 3; k <= p; ++k) {
+    sc[k] = sc[k - 2] / co[k - 2].c;
+    if (!std::isfinite(sc[k]) || std::fabs(sc[k]) > 0x1p60 || std::fabs(sc[k]) < 0x1p-60) return false;
+  }
+  return true;
+}
+
+// (alpha, beta, omega) of the fused step producing degree k (k >= 2): S_k = S_{k-2} + alpha A D^-1
+// S_{k-1} + beta S_{k-1} + omega W Lambda_{k-1}.
+static void fused_coefs(const std::vector<Coef>& co, const std::vector<double>& sc, int k, double* out) {
+  const Coef& q = co[k - 2];
+  out[0] = sc[k] * q.a / sc[k - 1];
+  out[1] = sc[k] * q.b / sc[k - 1];
+  out[2] = sc[k] * q.a;
 }
 
 static void check_bounds(double lmin, double lT, double lmax, int p) {
@@ -385,6 +408,35 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
   }
   RC_CHECK(prec == RCHFSI_FP32 || prec == RCHFSI_TF32 || prec == RCHFSI_BF16, RCHFSI_ERR_INVALID_ARG,
            "bad precision");
+  std::vector<double> sc;
+  if (!chfsi && fe_step_supported(f, N, prec) && fused_scales(co, sc)) {
+    // fused degree steps on scaled iterates: one tensor-core launch per step does the cell products,
+    // the recurrence terms and the update of R_X
+    float* RX = c.w.R32a.ensure(blk);
+    float* RY = c.w.R32b.ensure(blk);
+    float* Wl = c.w.W32.ensure(blk);
+    check_budget(c);
+    cast_f64_to_f32(c.s, blk, Wr, RY, s1 / e, 0);  // S_1 = R_1 = (sigma_1 / e) W
+    cast_f64_to_f32(c.s, blk, Wr, Wl, 1.0, 0);
+    fill_zero(c.s, RX, blk * sizeof(float));       // S_0 = R_0 = 0
+    if (!co.empty()) {
+      const int BN = fe_step_tune(c.s, c.num_sms, f, N, RY, Wl, lamtab + N);
+      for (int k = 2; k <= p; ++k) {
+        double cf[3];
+        fused_coefs(co, sc, k, cf);
+        FeStepPart parts[4];
+        const int np = fe_step_parts(f, RY, Wl, RX, lamtab + (size_t)(k - 1) * N, N, (float)cf[0], (float)cf[1],
+                                     (float)cf[2], nullptr, parts);
+        fe_step_batch(c.s, parts, np, BN, c.num_sms);
+        std::swap(RX, RY);
+      }
+    }
+    cast_f32_to_f64(c.s, blk, RY, Wr, 1.0 / sc[p]);  // R_p = S_p / s_p
+    transpose_f64(c.s, m, N, Wr, N, Y, m);
+    reconstruct_f64(c.s, m, N, Y, m, f.Dinv.p, X, lamtab + (size_t)p * N, Y);
+    c.last_applies = (int64_t)co.size();
+    return;
+  }
   float* RX = c.w.R32a.ensure(blk);
   float* RY = c.w.R32b.ensure(blk);
   float* Wl = c.w.W32.ensure(blk);
@@ -516,10 +568,20 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     RC_CHECK(fe_batchable(*j.c, p) && j.c->p.precision == prec, RCHFSI_ERR_UNSUPPORTED,
              "batched filter: FE operators, R-ChFSI, one TF32/BF16 precision and degree");
   const int nj = (int)jobs.size();
-  std::vector<std::vector<double>> tabs(nj), coefs(nj);
+  std::vector<std::vector<double>> tabs(nj), coefs(nj), scales(nj);
   std::vector<float*> RX(nj), RY(nj), WL(nj);
   std::vector<int> nn(nj), bn(nj);
   std::vector<double*> dtab(nj), dcoef(nj);
+  std::vector<std::vector<Coef>> cos(nj);
+  // fused degree steps (scaled iterates, one tensor-core launch per step) when every problem allows
+  bool fused = true;
+  for (int q = 0; q < nj; ++q) {
+    rchfsi_ctx& c = *jobs[q].c;
+    const int n = c.cplx ? c.Nc : c.p.block;
+    double e, cc, s1;
+    filter_scalars(jobs[q].lmin, jobs[q].lT, jobs[q].lmax, p, e, cc, s1, cos[q]);
+    fused = fused && fe_step_supported(*c.fe, n, prec) && fused_scales(cos[q], scales[q]);
+  }
   // 1. per problem: scalars, Lambda table and coefficient table on the device, initial blocks
   for (int q = 0; q < nj; ++q) {
     FeFilterJob& J = jobs[q];
@@ -535,6 +597,10 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     lambda_table(J.lam, n, e, cc, s1, co, tabs[q]);
     coefs[q].resize(3 * co.size());
     for (size_t k = 0; k < co.size(); ++k) {
+      if (fused) {
+        fused_coefs(co, scales[q], (int)k + 2, &coefs[q][3 * k]);
+        continue;
+      }
       coefs[q][3 * k] = co[k].a;
       coefs[q][3 * k + 1] = co[k].b;
       coefs[q][3 * k + 2] = co[k].c;
@@ -552,13 +618,26 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     cast_f64_to_f32(s, blk, Wr, RY[q], s1 / e, 0);
     cast_f64_to_f32(s, blk, Wr, WL[q], 1.0, 0);
     fill_zero(s, RX[q], blk * sizeof(float));
-    fe_tc_parts_prepare(s, *c.fe, prec);
+    if (fused) fe_step_prepare(s, *c.fe);
+    else fe_tc_parts_prepare(s, *c.fe, prec);
   }
-  // 2. column tiles (autotuned once per shape)
-  for (int q = 0; q < nj; ++q) bn[q] = tune_bn(s, num_sms, *jobs[q].c->fe, prec, nn[q], RY[q]);
-  // 3. the degree loop as one CUDA graph: per step, the recurrence terms of every problem and one
-  //    persistent tensor-core launch over every problem's cells (at most 64 parts per launch)
-  std::vector<uintptr_t> key = {(uintptr_t)p, (uintptr_t)prec};
+  // 2. column tiles (autotuned once per shape); the fused launch takes one tile for all problems,
+  //    the one tuned for the problem with the most cells
+  int bn_fused = 0;
+  int64_t most = -1;
+  for (int q = 0; q < nj; ++q) {
+    FeOp& op = *jobs[q].c->fe;
+    bn[q] = fused ? fe_step_tune(s, num_sms, op, nn[q], RY[q], WL[q], dtab[q] + nn[q])
+                  : tune_bn(s, num_sms, op, prec, nn[q], RY[q]);
+    if (op.n_cells * (op.cplx ? 4 : 1) > most) {
+      most = op.n_cells * (op.cplx ? 4 : 1);
+      bn_fused = bn[q];
+    }
+  }
+  // 3. the degree loop as one CUDA graph: per step one persistent tensor-core launch over every
+  //    problem's cells (at most 64 parts per launch); the unfused form runs the recurrence terms of
+  //    every problem first
+  std::vector<uintptr_t> key = {(uintptr_t)p, (uintptr_t)prec, (uintptr_t)fused};
   for (int q = 0; q < nj; ++q)
     for (uintptr_t v : {(uintptr_t)jobs[q].c, (uintptr_t)RX[q], (uintptr_t)RY[q], (uintptr_t)WL[q],
                         (uintptr_t)dtab[q], (uintptr_t)dcoef[q], (uintptr_t)nn[q], (uintptr_t)bn[q]})
@@ -574,7 +653,22 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     RC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
       std::vector<float*> rx = RX, ry = RY;
-      for (int k = 0; k + 1 < p; ++k) {
+      for (int k = 0; fused && k + 1 < p; ++k) {
+        std::vector<FeStepPart> parts;
+        for (int q = 0; q < nj; ++q) {
+          rchfsi_ctx& c = *jobs[q].c;
+          FeStepPart pp[4];
+          const int np = fe_step_parts(*c.fe, ry[q], WL[q], rx[q], dtab[q] + (size_t)(k + 1) * nn[q], nn[q], 0.f,
+                                       0.f, 0.f, dcoef[q] + 3 * k, pp);
+          parts.insert(parts.end(), pp, pp + np);
+        }
+        for (size_t o = 0; o < parts.size(); o += 64) {
+          fe_step_batch(s, parts.data() + o, (int)std::min<size_t>(64, parts.size() - o), bn_fused, num_sms);
+          ++kernels;
+        }
+        std::swap(rx, ry);
+      }
+      for (int k = 0; !fused && k + 1 < p; ++k) {
         std::vector<FeTcPart> parts;
         for (int q = 0; q < nj; ++q) {
           rchfsi_ctx& c = *jobs[q].c;
@@ -609,15 +703,16 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     plan.replays = 0;
   }
   {
-    const double fl = [&] {
-      double f = 0.0;
-      for (int q = 0; q < nj; ++q) {
-        const FeOp& op = *jobs[q].c->fe;
-        f += 2.0 * op.nc * op.nc * (double)op.n_cells * nn[q] * (op.cplx ? 4.0 : 1.0) * (p - 1);
-      }
-      return f;
-    }();
-    prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, fl, 0.0);
+    // algorithmic work of the replayed degree loop: per step and problem the cell products and the
+    // four block streams (R_Y, R_X read and written, W) plus the cell matrices of every real part
+    double fl = 0.0, by = 0.0;
+    for (int q = 0; q < nj; ++q) {
+      const FeOp& op = *jobs[q].c->fe;
+      const double parts = op.cplx ? 4.0 : 1.0;
+      fl += 2.0 * op.nc * op.nc * (double)op.n_cells * nn[q] * parts * (p - 1);
+      by += (16.0 * (double)jobs[q].c->p.m * nn[q] + 4.0 * op.nc * op.nc * (double)op.n_cells * parts) * (p - 1);
+    }
+    prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, fl, by);
     RC_CUDA(cudaGraphLaunch(plan.exec, s));
   }
   // launches inside the capture were counted once; count every later replay too
@@ -631,7 +726,7 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     const size_t blk = (size_t)m * n;
     float* ryf = ((p - 1) % 2 == 0) ? RY[q] : RX[q];
     double* Wr = c.w.stage_out.p;
-    cast_f32_to_f64(s, blk, ryf, Wr);
+    cast_f32_to_f64(s, blk, ryf, Wr, fused ? 1.0 / scales[q][p] : 1.0);  // fused: R_p = S_p / s_p
     transpose_f64(s, m, n, Wr, n, J.Y, m);
     reconstruct_f64(s, m, n, J.Y, m, c.fe->Dinv.p, J.X, dtab[q] + (size_t)p * n, J.Y);
     if (c.cplx) cplx_rebuild(s, c.mc, c.Nc, J.Y, nullptr, J.Y);

@@ -39,6 +39,9 @@ int64_t& launch_counter();
 // device, size) under a lock, so concurrent callers on any device never launch before it is set.
 void set_smem_limit(const void* kernel, int bytes);
 
+// The driver's cuTensorMapEncodeTiled (PFN_cuTensorMapEncodeTiled_v12000), looked up once.
+void* tensor_map_encoder();
+
 #define RC_LAUNCH()                                   \
   do {                                                \
     RC_CUDA(cudaGetLastError());                      \
@@ -130,7 +133,7 @@ void scale_rows_f64(cudaStream_t s, int64_t m, int64_t n, const double* in, doub
                     bool cols);  // out = diag(d)*in (cols=false) or in*diag(d) (cols=true); row-major m x n
 void cast_f64_to_f32(cudaStream_t s, int64_t n, const double* in, float* out, double scale, int round_tf32);
 void cast_f64_to_bf16(cudaStream_t s, int64_t n, const double* in, __nv_bfloat16* out, double scale);
-void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out);
+void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out, double scale = 1.0);
 void fill_zero(cudaStream_t s, void* p, size_t bytes);
 void scaled_copy_f64(cudaStream_t s, int64_t n, const double* in, double* out, double scale);
 // Yp(col) = dinv .* R + X .* lam  (R of type float/double, col-major m x n)

@@ -85,8 +85,9 @@ __global__ void cast_f64_bf16_kernel(int64_t n, const double* in, __nv_bfloat16*
     out[e] = __float2bfloat16_rn((float)(in[e] * scale));
 }
 
-__global__ void cast_f32_f64_kernel(int64_t n, const float* in, double* out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += grid_threads()) out[e] = in[e];
+__global__ void cast_f32_f64_kernel(int64_t n, const float* in, double* out, double scale) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += grid_threads())
+    out[e] = scale * (double)in[e];
 }
 
 __global__ void scaled_copy_kernel(int64_t n, const double* in, double* out, double scale) {
@@ -215,8 +216,8 @@ void cast_f64_to_bf16(cudaStream_t s, int64_t n, const double* in, __nv_bfloat16
   RC_LAUNCH();
 }
 
-void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out) {
-  cast_f32_f64_kernel<<<ew_blocks(n), 256, 0, s>>>(n, in, out);
+void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out, double scale) {
+  cast_f32_f64_kernel<<<ew_blocks(n), 256, 0, s>>>(n, in, out, scale);
   RC_LAUNCH();
 }
 

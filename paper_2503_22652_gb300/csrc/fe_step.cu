@@ -1,0 +1,542 @@
+// Fused degree step of the finite-element R-ChFSI filter (the loop body of Algorithm 3) on the
+// tcgen05 tensor cores, in one pass over the block.
+//
+// The recurrence R_k = a_k A D^-1 R_{k-1} + b_k R_{k-1} + c_k R_{k-2} + a_k W Lambda_{k-1} runs on
+// scaled iterates S_j = s_j R_j, with s_k = s_{k-2} / c_k chosen on the host, so that
+//   S_k = S_{k-2} + alpha A D^-1 S_{k-1} + beta S_{k-1} + omega W Lambda_{k-1},
+//   alpha = s_k a_k / s_{k-1},  beta = s_k b_k / s_{k-1},  omega = s_k a_k:
+// the old iterate enters with coefficient 1, so the whole step is additions into the buffer that
+// holds S_{k-2}.  The cell products are added with vector atomics (a dof shared by several cells
+// receives one add per cell); beta S_{k-1} + omega W Lambda is added once per dof, by the cell that
+// owns it (the first cell, in cell order, that contains it).  Each of S_{k-1}, S_{k-2} and W is
+// then read once and S_k written once per step, the four block streams of the algorithm, plus
+// the cell matrices.
+//
+// Per (cell, column tile): D (128 x BN, FP32 in TMEM) = (A_c D_c^-1) (128 x 128: the cell matrix
+// with its columns scaled by D^-1 at the cell's dofs, padded from n_c <= 128, packed once per
+// operator as a K-major 128-byte-swizzled TF32 image) x V_c (128 x BN: the cell's rows of S_{k-1}).
+// V_c is gathered from the row-major block by TMA (tile::gather4: four rows of 32 columns per
+// copy) straight into the MN-major 128-byte-swizzled layout that the MMA reads (the 32 columns of
+// a row contiguous, 8 rows per 1024-byte atom), so no thread touches the operand: the MMA reads the
+// stored FP32 values as TF32.
+//
+// Warp roles (320 threads):
+//   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile, lane l
+//              issues BN/32 gather4 copies of the cell's nodes 4l..4l+3 into a ring of stages;
+//   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), two TMEM
+//              accumulators of BN columns;
+//   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4).. (one cell node per thread) and half
+//              of the tile's columns; it scales by alpha, adds the owner terms (the row's S_{k-1}
+//              and W values, loaded before it waits for the accumulator) and scatter-adds with
+//              red.global.add.v4.f32.
+// Every mbarrier wait is bounded; on a timeout the kernel raises the error flag, waits (bounded)
+// for its copies and MMAs in flight, releases TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "fe_step.cuh"
+#include "prof.cuh"
+#include "tc_ptx.cuh"
+
+namespace rchfsi {
+namespace {
+
+constexpr int kNCP = 128;                       // padded cell size (MMA M and K)
+constexpr int kThreads = 320;                   // 10 warps
+constexpr uint32_t kABytes = kNCP * kNCP * 4;   // TF32 cell image
+constexpr uint32_t kChunkBytes = kNCP * 128;    // 32 columns of V_c: 128 rows of 128 bytes
+constexpr int kMaxParts = 64;
+constexpr int kSmemMax = 232448;                // dynamic + static shared memory per CTA
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (row r, k) of a 128 x 128 K-major 128-byte-swizzled FP32 image.
+__device__ __forceinline__ uint32_t sw_off4(int r, int k) {
+  const int kb = k >> 5, byte = (k & 31) * 4;
+  const int chunk = (byte >> 4) ^ (r & 7);
+  return (uint32_t)kb * kNCP * 128 + (uint32_t)r * 128 + (chunk << 4) + (byte & 15);
+}
+
+// (A_c D_c^-1) images: column k of cell c scaled by dinv[dofs(c, k)], rounded to TF32.
+__global__ void pack_scaled_kernel(int64_t n_cells, int nc, const double* __restrict__ A, const int* __restrict__ dofs,
+                                   const double* __restrict__ dinv, uint8_t* __restrict__ img) {
+  const int64_t per_cell = (int64_t)kNCP * kNCP;
+  const int64_t total = n_cells * per_cell;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / per_cell;
+    const int r = (int)((e % per_cell) / kNCP), k = (int)(e % kNCP);
+    const double v = (r < nc && k < nc) ? A[(c * nc + r) * nc + k] * dinv[dofs[c * nc + k]] : 0.0;
+    *reinterpret_cast<float*>(img + c * per_cell * 4 + sw_off4(r, k)) = tf32_rna((float)v);
+  }
+}
+
+struct StepPartDev {
+  CUtensorMap vmap;       // rows of V: 2D {n, rows}, box {32, 1}, 128-byte swizzle, zero fill
+  const int* dofs;
+  const uint32_t* own;    // 4 words per cell (bit i: the cell owns its node i); null: no owner terms
+  const uint8_t* img;
+  const float* V;
+  const float* W;
+  float* U;
+  const double* lam;
+  const double* coef;
+  int64_t n_cells, cell_off;
+  float alpha, beta, omega, sign;
+  int nc, n, ntiles;
+};
+
+struct StepBatch {
+  StepPartDev part[kMaxParts];
+  int64_t total_cells;
+  int nparts, nA, nslots;
+  uint32_t tmem_cols;
+  int* err;
+};
+
+__device__ __forceinline__ int part_of(const StepBatch& p, int64_t g) {
+  int q = 0;
+  while (q + 1 < p.nparts && g >= p.part[q + 1].cell_off) ++q;
+  return q;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+
+// Four rows (r0..r3) of 32 columns starting at column x, into 512 consecutive bytes of shared memory.
+__device__ __forceinline__ void gather4(void* dst, const CUtensorMap* map, int x, int r0, int r1, int r2, int r3,
+                                        uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];" ::"r"(tc::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// Descriptor of an MN-major operand with 128-byte swizzle: 8 K-rows of 128 bytes per 1024-byte
+// atom (stride byte offset 1024 between atoms along K), 32-element column chunks `lbo` bytes apart
+// (leading byte offset).
+__device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t smem_addr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_constant__ StepBatch p) {
+  constexpr int NCH = BN / 32;
+  constexpr uint32_t kSlotBytes = NCH * kChunkBytes;
+  constexpr int HB = BN / 2;  // columns of one epilogue thread per tile
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[4], bempty[4], accfull[2], accempty[2], mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + (size_t)p.nA * kABytes;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&afull[i], 1);
+      tc::mbar_init(&aempty[i], 1);
+      tc::mbar_init(&accfull[i], 1);
+      tc::mbar_init(&accempty[i], 256);
+    }
+    for (int i = 0; i < 4; ++i) {
+      tc::mbar_init(&bfull[i], 1);
+      tc::mbar_init(&bempty[i], 1);
+    }
+    tc::mbar_init(&mma_done, 1);
+    tc::fence_barrier_init();
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&tmem_slot, p.tmem_cols);
+    tc::tmem_relinquish();
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* vabort = &abort_flag;
+  auto fail = [&]() {
+    *vabort = 1;
+    atomicExch(p.err, 1);
+  };
+  const int64_t G = gridDim.x;
+  const int nA = p.nA, nS = p.nslots;
+
+  if (warp == 0) {
+    // ---------------- loader
+    int64_t j = 0, cl = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
+      const StepPartDev& P = p.part[part_of(p, g)];
+      const int64_t cell = g - P.cell_off;
+      int r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) r[u] = __ldg(P.dofs + cell * P.nc + min(4 * lane + u, P.nc - 1));
+      const int ab = (int)(cl % nA);
+      int ok = 1;
+      if (lane == 0) {
+        ok = !*vabort && tc::mbar_wait(&aempty[ab], (uint32_t)((cl / nA) & 1) ^ 1u);
+        if (ok) {
+          tc::mbar_arrive_expect_tx(&afull[ab], kABytes);
+          bulk_g2s(sA + (size_t)ab * kABytes, P.img + cell * (int64_t)kABytes, kABytes, &afull[ab]);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) fail();
+        stop = true;
+        break;
+      }
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int s = (int)(j % nS);
+        if (lane == 0) {
+          ok = !*vabort && tc::mbar_wait(&bempty[s], (uint32_t)((j / nS) & 1) ^ 1u);
+          if (ok) tc::mbar_arrive_expect_tx(&bfull[s], kSlotBytes);
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) fail();
+          stop = true;
+          break;
+        }
+        uint8_t* dst = sB + (size_t)s * kSlotBytes + lane * 512;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) gather4(dst + c * kChunkBytes, &P.vmap, t * BN + 32 * c, r[0], r[1], r[2], r[3], &bfull[s]);
+      }
+    }
+    if (*vabort && lane == 0) {
+      // let the copies already issued land before the CTA's shared memory is released (bounded)
+      for (int64_t c2 = (cl > nA ? cl - nA : 0); c2 < cl; ++c2) tc::mbar_wait(&afull[c2 % nA], (uint32_t)((c2 / nA) & 1));
+      for (int64_t j2 = (j > nS ? j - nS : 0); j2 < j; ++j2) tc::mbar_wait(&bfull[j2 % nS], (uint32_t)((j2 / nS) & 1));
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    const bool leader = tc::elect_one();
+    constexpr uint32_t idesc = tc::instr_desc(2u, kNCP, BN) | (1u << 16);  // TF32, B MN-major
+    int64_t j = 0, cl = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
+      const StepPartDev& P = p.part[part_of(p, g)];
+      const int ab = (int)(cl % nA);
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int s = (int)(j % nS), xb = (int)(j & 1);
+        bool ok = !*vabort;
+        if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl / nA) & 1));
+        if (ok) ok = tc::mbar_wait(&bfull[s], (uint32_t)((j / nS) & 1));
+        if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (leader) fail();
+          stop = true;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint64_t a0 = tc::sw128_desc(tc::smem_u32(sA + (size_t)ab * kABytes));
+        const uint64_t b0 = mn_sw128_desc(tc::smem_u32(sB + (size_t)s * kSlotBytes), kChunkBytes);
+        const uint32_t d = tmem + (uint32_t)(xb * BN);
+#pragma unroll
+        for (int kk = 0; kk < kNCP / 8; ++kk) {
+          const int kel = kk * 8;
+          const uint32_t aoff = (uint32_t)(kel >> 5) * kNCP * 128 + (uint32_t)((kel & 31) * 4);
+          if (leader) tc::mma_tf32(d, tc::desc_add(a0, aoff), tc::desc_add(b0, (uint32_t)kk * 1024u), idesc, kk > 0 ? 1u : 0u);
+        }
+        __syncwarp();
+        if (leader) {
+          tc::mma_commit(&bempty[s]);
+          tc::mma_commit(&accfull[xb]);
+          if (t == P.ntiles - 1) tc::mma_commit(&aempty[ab]);
+        }
+        __syncwarp();
+      }
+    }
+    // every MMA issued has completed before TMEM is released
+    if (leader) {
+      tc::mma_commit(&mma_done);
+      tc::mbar_wait(&mma_done, 0u);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;       // column half of the tile
+    const int i = q * 32 + lane;         // cell-local node of this thread's accumulator row
+    int64_t j = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
+      const StepPartDev& P = p.part[part_of(p, g)];
+      const int64_t cell = g - P.cell_off;
+      float al = P.alpha, be = P.beta, om = P.omega;
+      if (P.coef) {
+        al = (float)__ldg(P.coef);
+        be = (float)__ldg(P.coef + 1);
+        om = (float)__ldg(P.coef + 2);
+      }
+      al *= P.sign;
+      int64_t row = -1;
+      bool own = false;
+      if (i < P.nc) {
+        row = (int64_t)__ldg(P.dofs + cell * P.nc + i) * P.n;
+        own = P.own && ((__ldg(P.own + cell * 4 + (i >> 5)) >> (i & 31)) & 1u);
+      }
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int xb = (int)(j & 1);
+        const int c0 = t * BN + h * HB;
+        // owner terms: this row's S_{k-1} and W values, in flight while the MMA finishes
+        float4 vv[HB / 4], ww[HB / 4];
+        if (own) {
+#pragma unroll
+          for (int u = 0; u < HB / 4; ++u) {
+            const int col = c0 + 4 * u;
+            if (col < P.n) {
+              vv[u] = __ldg(reinterpret_cast<const float4*>(P.V + row + col));
+              ww[u] = __ldg(reinterpret_cast<const float4*>(P.W + row + col));
+            }
+          }
+        }
+        bool ok = !*vabort && tc::mbar_wait(&accfull[xb], (uint32_t)((j >> 1) & 1));
+        if (!ok) fail();
+        if (!__all_sync(0xffffffffu, ok && !*vabort)) {
+          stop = true;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * BN + h * HB);
+#pragma unroll
+        for (int cc = 0; cc < HB; cc += 16) {
+          float v[16];
+          tc::tmem_ld16(taddr + cc, v);
+          if (row >= 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int col = c0 + cc + 4 * u;
+              if (col < P.n) {
+                float o0 = al * v[4 * u], o1 = al * v[4 * u + 1], o2 = al * v[4 * u + 2], o3 = al * v[4 * u + 3];
+                if (own) {
+                  const float4 x = vv[(cc >> 2) + u], w = ww[(cc >> 2) + u];
+                  o0 += be * x.x + om * (float)__ldg(P.lam + col) * w.x;
+                  o1 += be * x.y + om * (float)__ldg(P.lam + col + 1) * w.y;
+                  o2 += be * x.z + om * (float)__ldg(P.lam + col + 2) * w.z;
+                  o3 += be * x.w + om * (float)__ldg(P.lam + col + 3) * w.w;
+                }
+                red_add_v4(P.U + row + col, o0, o1, o2, o3);
+              }
+            }
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&accempty[xb]);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, p.tmem_cols);
+  }
+}
+
+// Shared-memory plan of a tile width: cell-image buffers and stages that fit.
+struct Plan {
+  int nA, nslots;
+  size_t smem;
+};
+
+Plan make_plan(int BN) {
+  const size_t slot = (size_t)(BN / 32) * kChunkBytes;
+  const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
+  for (int nA : {2, 1})
+    for (int ns : {4, 3, 2}) {
+      const size_t need = (size_t)nA * kABytes + (size_t)ns * slot;
+      if (need <= cap) return Plan{nA, ns, need + 1024};
+    }
+  return Plan{0, 0, 0};
+}
+
+CUtensorMap row_map(const float* base, int64_t rows, int n) {
+  CUtensorMap m;
+  RC_CHECK(((uintptr_t)base & 15) == 0 && n % 4 == 0, RCHFSI_ERR_INVALID_ARG,
+           "fused FE step: block rows must start on 16-byte boundaries");
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)n * 4};
+  cuuint32_t box[2] = {32, 1};
+  cuuint32_t estr[2] = {1, 1};
+  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  RC_CHECK(r == CUDA_SUCCESS, RCHFSI_ERR_CUDA, "cuTensorMapEncodeTiled (gather map) failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+const uint8_t* scaled_images(cudaStream_t s, FeOp& op, const double* dinv) {
+  if (!op.imgADtf.p) {
+    op.imgADtf.ensure((size_t)kABytes * op.n_cells);
+    const int64_t total = op.n_cells * (int64_t)kNCP * kNCP;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    pack_scaled_kernel<<<blocks, 256, 0, s>>>(op.n_cells, op.nc, op.A64.p, op.dofs.p, dinv, op.imgADtf.p);
+    RC_LAUNCH();
+  }
+  return op.imgADtf.p;
+}
+
+template <int BN>
+void launch(cudaStream_t s, const StepBatch& b, const Plan& pl, unsigned grid) {
+  set_smem_limit(reinterpret_cast<const void*>(fe_step_kernel<BN>), kSmemMax - 512);
+  fe_step_kernel<BN><<<grid, kThreads, pl.smem, s>>>(b);
+  RC_LAUNCH();
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int, int>, int> g_tune;
+
+}  // namespace
+
+bool fe_step_supported(const FeOp& op, int n, int precision) {
+  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own.p != nullptr;
+}
+
+void fe_step_prepare(cudaStream_t s, FeOp& op) {
+  scaled_images(s, op, op.Dinv.p);
+  if (op.cplx) scaled_images(s, *op.imag, op.Dinv.p);
+}
+
+int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const double* lam, int n, float alpha,
+                  float beta, float omega, const double* coef, FeStepPart* out) {
+  if (!op.cplx) {
+    out[0] = FeStepPart{&op, V, W, U, lam, coef, op.m, n, alpha, beta, omega, 1.f, true};
+    return 1;
+  }
+  // complex operator on the real embedding: rows [0, mc) real parts, [mc, 2 mc) imaginary parts
+  //   U_r += alpha (Ar V_r - Ai V_i),   U_i += alpha (Ai V_r + Ar V_i)
+  // and the owner terms of each half once (with the Ar part of that half)
+  const int64_t mc = op.mc, off = mc * (int64_t)n;
+  FeOp& im = *op.imag;
+  out[0] = FeStepPart{&op, V, W, U, lam, coef, mc, n, alpha, beta, omega, 1.f, true};
+  out[1] = FeStepPart{&im, V + off, W, U, lam, coef, mc, n, alpha, beta, omega, -1.f, false};
+  out[2] = FeStepPart{&im, V, W, U + off, lam, coef, mc, n, alpha, beta, omega, 1.f, false};
+  out[3] = FeStepPart{&op, V + off, W + off, U + off, lam, coef, mc, n, alpha, beta, omega, 1.f, true};
+  return 4;
+}
+
+void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, int num_sms) {
+  RC_CHECK(nparts >= 1 && nparts <= kMaxParts, RCHFSI_ERR_INVALID_ARG, "fused FE step: 1..64 parts per launch");
+  RC_CHECK(BN == 32 || BN == 64 || BN == 96 || BN == 128, RCHFSI_ERR_INVALID_ARG,
+           "fused FE step: column tile of 32, 64, 96 or 128");
+  const Plan pl = make_plan(BN);
+  RC_CHECK(pl.nA > 0, RCHFSI_ERR_INVALID_ARG, "fused FE step: no shared-memory plan for this tile");
+  StepBatch b{};
+  b.nparts = nparts;
+  b.nA = pl.nA;
+  b.nslots = pl.nslots;
+  int64_t off = 0;
+  double flops = 0.0, bytes = 0.0;
+  for (int q = 0; q < nparts; ++q) {
+    const FeStepPart& t = parts[q];
+    FeOp& op = *t.op;
+    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own.p, RCHFSI_ERR_INVALID_ARG,
+             "fused FE step: n_c <= 128, n a multiple of 4 and owner masks required");
+    StepPartDev& P = b.part[q];
+    P.vmap = row_map(t.V, t.rows, t.n);
+    P.dofs = op.dofs.p;
+    P.own = t.owner ? op.own.p : nullptr;
+    // the scaled images use the D^-1 of the rows the part reads (both halves share it)
+    P.img = scaled_images(s, op, op.Dinv.p);
+    P.V = t.V;
+    P.W = t.W;
+    P.U = t.U;
+    P.lam = t.lam;
+    P.coef = t.coef;
+    P.n_cells = op.n_cells;
+    P.cell_off = off;
+    P.alpha = t.alpha;
+    P.beta = t.beta;
+    P.omega = t.omega;
+    P.sign = t.sign;
+    P.nc = op.nc;
+    P.n = t.n;
+    P.ntiles = (t.n + BN - 1) / BN;
+    off += op.n_cells;
+    const double nc = op.nc, C = (double)op.n_cells;
+    flops += 2.0 * nc * nc * C * t.n;
+    // algorithmic bytes: the cell images, and for the owner part of each row half the four block
+    // streams (V read, U read and written, W read); a complex operator's cross parts re-read V
+    bytes += 4.0 * nc * nc * C + (t.owner ? 16.0 * (double)t.rows * t.n : 0.0);
+  }
+  b.total_cells = off;
+  b.err = parts[0].op->err;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * BN)) cols <<= 1;
+  b.tmem_cols = cols;
+  const unsigned grid = (unsigned)std::min<int64_t>(b.total_cells, (int64_t)num_sms);
+  prof::Scope ps(s, RCHFSI_KERNEL_FE_CELL, flops, bytes);
+  switch (BN) {
+    case 32: launch<32>(s, b, pl, grid); break;
+    case 64: launch<64>(s, b, pl, grid); break;
+    case 96: launch<96>(s, b, pl, grid); break;
+    default: launch<128>(s, b, pl, grid); break;
+  }
+}
+
+int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, const float* W, const double* lam) {
+  const auto key = std::make_tuple(op.nc, (int64_t)op.n_cells, n, op.cplx ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  std::vector<int> cand;
+  for (int bn : {32, 64, 96, 128})
+    if (bn <= std::max(32, (n + 31) / 32 * 32)) cand.push_back(bn);
+  DevBuf<float> scratch;
+  float* out = scratch.ensure((size_t)op.m * n);
+  cudaEvent_t e0, e1;
+  RC_CUDA(cudaEventCreate(&e0));
+  RC_CUDA(cudaEventCreate(&e1));
+  int best = cand[0];
+  float best_ms = 1e30f;
+  for (int bn : cand) {
+    FeStepPart parts[4];
+    const int np = fe_step_parts(op, V, W, out, lam, n, 1.f, 0.5f, 0.25f, nullptr, parts);
+    fe_step_batch(s, parts, np, bn, num_sms);  // warm-up
+    RC_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 2; ++r) fe_step_batch(s, parts, np, bn, num_sms);
+    RC_CUDA(cudaEventRecord(e1, s));
+    RC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
+}  // namespace rchfsi

@@ -312,6 +312,8 @@ void run(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64_t K, const T* 
 
 }  // namespace
 
+void* tensor_map_encoder() { return reinterpret_cast<void*>(encode_fn()); }
+
 void tc_gemm_tf32_recur(cudaStream_t s, int num_sms, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                         const float* B, int64_t ldb, DevBuf<float>& split, const TcRecur& r, int64_t ldo, int* err) {
   Epi<float> e{r.a, r.b, r.c, r.Ry, r.Rx, r.W, r.lam, r.out, ldo};

@@ -28,7 +28,8 @@ def _indefinite_pencil(m=200, seed=5):
     q = wl.orthogonal(m, seed)
     A = wl.dense_from_spectrum(q, np.linspace(-1.0, 10.0, m))
     mu = np.linspace(1.0, 3.0, m)
-    mu[::5] = -1.0                     # every fifth eigenvalue of B negative
+    mu[: m // 2] = -3.0                # half the spectrum of B negative: tr(B) < 0, so the Gram
+                                       # matrix of any block is indefinite with high probability
     B = wl.dense_from_spectrum(wl.orthogonal(m, seed + 1), mu)
     return A, B
 
