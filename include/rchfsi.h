@@ -159,6 +159,8 @@ typedef struct rchfsi_stats {
   int64_t operator_applies;/* block operator products done by the filters */
   double* history;         /* optional caller array of max_iter+1 doubles: max relative residual
                               before each filter (may be NULL) */
+  int32_t cholqr_retries;  /* Rayleigh-Ritz steps whose Gram matrix G_B had no Cholesky factor and
+                              that went through the shifted Cholesky QR step (real problems) */
 } rchfsi_stats;
 
 /* ---------------------------------------------------------------- lifecycle */
@@ -212,7 +214,11 @@ int rchfsi_residual(struct rchfsi_ctx* h, const double* X, const double* Lambda,
 /* Rayleigh-Ritz for a non-orthogonal basis (Section 2.1, Algorithm 1 steps 2-3), FP64:
  * columns of Y scaled to unit norm, G_A = Y^T A Y, G_B = Y^T B Y, Cholesky G_B = L L^T, eigen-
  * decomposition of L^-1 G_A L^-T, X = Y L^-T V (B-orthonormal), evals ascending.
- * Errors: ILL_CONDITIONED when G_B is not numerically positive definite. */
+ * When G_B has no Cholesky factor (a numerically rank-deficient basis), a real problem's basis is
+ * first preconditioned by one shifted Cholesky QR step in the B inner product (Y <- Y L_s^-T,
+ * L_s L_s^T = G_B + s I, s = 11 (m N + N (N + 1)) 2^-53 tr(G_B)) and the Gram matrices are formed
+ * again.  Errors: ILL_CONDITIONED when G_B (after that step) is not numerically positive definite,
+ * e.g. an indefinite B. */
 int rchfsi_rayleigh_ritz(struct rchfsi_ctx* h, const double* Y, double* X, double* evals);
 
 /* k-step Lanczos (no re-orthogonalisation) on D^-1/2 A D^-1/2 from start vector v0 (m doubles):

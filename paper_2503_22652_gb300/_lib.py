@@ -60,7 +60,8 @@ class rchfsi_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("max_rel_residual", C.c_double),
                 ("max_abs_residual", C.c_double), ("lmax", C.c_double), ("normA", C.c_double),
                 ("t_total_ms", C.c_double), ("t_filter_ms", C.c_double), ("t_rr_ms", C.c_double),
-                ("filter_flops", C.c_double), ("operator_applies", C.c_int64), ("history", C.c_void_p)]
+                ("filter_flops", C.c_double), ("operator_applies", C.c_int64), ("history", C.c_void_p),
+                ("cholqr_retries", C.c_int32)]
 
 
 class rchfsi_request(C.Structure):

@@ -488,7 +488,7 @@ struct SolveRun {
   int N = 0, nev = 0, Nout = 0;
   double lmax = 0.0, normA = 1.0;
   std::vector<double> ev, ra, xn;
-  int rc = RCHFSI_OK, it = 0, best_it = 0;
+  int rc = RCHFSI_OK, it = 0, best_it = 0, retries = 0;
   double best = INFINITY, maxrel = INFINITY, maxabs = INFINITY;
   int64_t applies = 0;
   double flops = 0.0, t_filter = 0.0, t_rr = 0.0;
@@ -530,6 +530,7 @@ void run_begin(SolveRun& r) {
   RC_CHECK(r.normA > 0.0 && std::isfinite(r.normA), RCHFSI_ERR_NUMERIC, "||A|| estimate is not positive");
   const auto tr = std::chrono::steady_clock::now();
   r.rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
+  r.retries += c.rr_retries;
   pair_after_rr(r);
   r.t_rr += ms_since(tr);
 }
@@ -598,6 +599,7 @@ void run_rr(SolveRun& r) {
   rchfsi_ctx& c = *r.h;
   const auto tr = std::chrono::steady_clock::now();
   r.rc = rayleigh_ritz(c, c.w.Y.p, c.w.X.p, c.w.AX.p, c.w.BX.p, c.w.evals.p);
+  r.retries += c.rr_retries;
   pair_after_rr(r);
   r.t_rr += ms_since(tr);
   ++r.it;
@@ -626,6 +628,7 @@ void run_end(SolveRun& r) {
     r.st->t_rr_ms = r.t_rr;
     r.st->filter_flops = r.flops;
     r.st->operator_applies = r.applies;
+    r.st->cholqr_retries = r.retries;
   }
 }
 

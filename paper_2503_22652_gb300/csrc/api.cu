@@ -796,56 +796,84 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   auto jcomplete = [&](double* Z) {
     if (c.cplx) cplx_rebuild(c.s, c.mc, c.Nc, Z, nullptr, Z);
   };
-  if (emu) {
-    // FP64-accurate products from BF16 slices: Y as N logical rows of length m
-    oz_slice(c.s, Na, m, Y, m, 1, w.ozL);
-    if (c.op_kind == RCHFSI_OP_DENSE) {
-      DenseOp& d = c.dense;
-      if (d.ozA.R != m) oz_slice(c.s, m, m, d.A.p, m, 1, d.ozA);
-      oz_gemm(c.s, c.num_sms, d.ozA, w.ozL, AY, m, w.ozws, eflag);
-      jcomplete(AY);
-      if (d.has_B) {
-        if (d.ozB.R != m) oz_slice(c.s, m, m, d.B.p, m, 1, d.ozB);
-        oz_gemm(c.s, c.num_sms, d.ozB, w.ozL, BY, m, w.ozws, eflag);
-        jcomplete(BY);
+  // A Y, B Y and the Gram matrices G_A = Y^T A Y, G_B = Y^T B Y of the current Y
+  auto grams = [&]() {
+    if (emu) {
+      // FP64-accurate products from BF16 slices: Y as N logical rows of length m
+      oz_slice(c.s, Na, m, Y, m, 1, w.ozL);
+      if (c.op_kind == RCHFSI_OP_DENSE) {
+        DenseOp& d = c.dense;
+        if (d.ozA.R != m) oz_slice(c.s, m, m, d.A.p, m, 1, d.ozA);
+        oz_gemm(c.s, c.num_sms, d.ozA, w.ozL, AY, m, w.ozws, eflag);
+        jcomplete(AY);
+        if (d.has_B) {
+          if (d.ozB.R != m) oz_slice(c.s, m, m, d.B.p, m, 1, d.ozB);
+          oz_gemm(c.s, c.num_sms, d.ozB, w.ozL, BY, m, w.ozws, eflag);
+          jcomplete(BY);
+        } else {
+          RC_CUDA(cudaMemcpyAsync(BY, Y, sizeof(double) * m * N, cudaMemcpyDeviceToDevice, c.s));
+        }
       } else {
-        RC_CUDA(cudaMemcpyAsync(BY, Y, sizeof(double) * m * N, cudaMemcpyDeviceToDevice, c.s));
+        apply_A_f64(c, Y, AY, Na);
+        jcomplete(AY);
+        apply_B_f64(c, Y, BY, Na);
+        jcomplete(BY);
       }
+      if (Na != N) oz_slice(c.s, N, m, Y, m, 1, w.ozL);  // every column for the Gram matrices
+      // G_A = Y^T A Y, G_B = Y^T B Y (complex: the left N x Na half; the rest follows from J)
+      oz_slice(c.s, Na, m, AY, m, 1, w.ozR);
+      oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GA.p, N, w.ozws, eflag);
+      oz_slice(c.s, Na, m, BY, m, 1, w.ozR);
+      oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag);
     } else {
       apply_A_f64(c, Y, AY, Na);
       jcomplete(AY);
       apply_B_f64(c, Y, BY, Na);
       jcomplete(BY);
+      // G_A = Y^T A Y, G_B = Y^T B Y  (N x Na, column-major)
+      gemm_f64(c.s, N, Na, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
+      gemm_f64(c.s, N, Na, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
     }
-    if (Na != N) oz_slice(c.s, N, m, Y, m, 1, w.ozL);  // every column for the Gram matrices
-    // G_A = Y^T A Y, G_B = Y^T B Y (complex: the left N x Na half; the rest follows from J)
-    oz_slice(c.s, Na, m, AY, m, 1, w.ozR);
-    oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GA.p, N, w.ozws, eflag);
-    oz_slice(c.s, Na, m, BY, m, 1, w.ozR);
-    oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag);
-  } else {
-    apply_A_f64(c, Y, AY, Na);
-    jcomplete(AY);
-    apply_B_f64(c, Y, BY, Na);
-    jcomplete(BY);
-    // G_A = Y^T A Y, G_B = Y^T B Y  (N x Na, column-major)
-    gemm_f64(c.s, N, Na, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
-    gemm_f64(c.s, N, Na, m, Y, m, true, BY, m, true, epi_store(w.GB.p, N));
-  }
-  if (c.cplx) {
-    cplx_gram_complete(c.s, c.Nc, w.GA.p);
-    cplx_gram_complete(c.s, c.Nc, w.GB.p);
-  }
-  {
-    // G_B = L L^T and L^-1 (one cluster / cooperative kernel)
+    if (c.cplx) {
+      cplx_gram_complete(c.s, c.Nc, w.GA.p);
+      cplx_gram_complete(c.s, c.Nc, w.GB.p);
+    }
+  };
+  // G_B = L L^T and L^-1 (one cluster / cooperative kernel); G_B is kept in Zt for a retry
+  auto factor = [&]() {
     prof::Scope ps(c.s, RCHFSI_KERNEL_SMALL_DENSE, 2.0 * N * N * N / 3.0, 8.0 * N * N * 3);
     symmetrize_f64(c.s, N, w.GA.p, N);
     symmetrize_f64(c.s, N, w.GB.p, N);
+    RC_CUDA(cudaMemcpyAsync(w.Zt.p, w.GB.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));
     cholesky_inverse_f64(c.s, N, w.GB.p, w.Lb.p, w.Li.p, w.info.p, c.num_sms, w.eigws);
+    int inf = 0;
+    RC_CUDA(cudaMemcpyAsync(&inf, w.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    return inf;
+  };
+  grams();
+  int info = factor();
+  c.rr_retries = 0;
+  if (info != 0 && !c.cplx) {
+    // The basis is numerically rank deficient for the Cholesky factorisation of its Gram matrix
+    // (Section 2.1 Rayleigh-Ritz of a non-orthogonal basis): precondition it by one shifted
+    // Cholesky QR step in the B inner product, Y <- Y L_s^-T with L_s L_s^T = G_B + s I and
+    // s = 11 (m N + N (N + 1)) u tr(G_B) (the shift of Fukaya et al.'s shifted CholeskyQR, with the
+    // trace bounding ||B^1/2 Y||_2^2), then form the products and Gram matrices of the new basis
+    // again; the Cholesky factorisation of that Gram matrix is the second CholeskyQR pass.
+    const double u = std::ldexp(1.0, -53);
+    shift_diag_by_trace_f64(c.s, N, w.Zt.p, N, 11.0 * ((double)m * N + (double)N * (N + 1)) * u);
+    cholesky_inverse_f64(c.s, N, w.Zt.p, w.Lb.p, w.Li.p, w.info.p, c.num_sms, w.eigws);
+    RC_CUDA(cudaMemcpyAsync(&info, w.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+    RC_CUDA(cudaStreamSynchronize(c.s));
+    if (info != 0) return RCHFSI_ERR_ILL_CONDITIONED;
+    // Y <- Y L_s^-T (column-major m x N times the transpose of the lower-triangular inverse)
+    gemm_f64(c.s, m, N, N, Y, m, false, w.Li.p, N, false, epi_store(w.T1.p, m));
+    RC_CUDA(cudaMemcpyAsync(Y, w.T1.p, sizeof(double) * m * N, cudaMemcpyDeviceToDevice, c.s));
+    grams();
+    info = factor();
+    c.rr_retries = 1;
   }
-  int info = 0;
-  RC_CUDA(cudaMemcpyAsync(&info, w.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
-  RC_CUDA(cudaStreamSynchronize(c.s));
   if (info != 0) return RCHFSI_ERR_ILL_CONDITIONED;
   // M = L^-1 G_A L^-T (two FP64 GEMMs on all SMs)
   {

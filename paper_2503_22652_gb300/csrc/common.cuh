@@ -158,6 +158,8 @@ void resid_rel_norms(cudaStream_t s, int64_t m, int64_t n, const double* W, cons
 
 // Small dense FP64 kernels (N x N, column-major).
 void symmetrize_f64(cudaStream_t s, int n, double* A, int lda);
+// A += factor * tr(A) * I (n x n, leading dimension lda)
+void shift_diag_by_trace_f64(cudaStream_t s, int n, double* A, int lda, double factor);
 // Cholesky G = L L^T and L^-1 (small_eig.cu): A (n x n, col-major) destroyed; L, Linv lower triangular.
 int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Linv, int* d_info, int num_sms,
                          DevBuf<double>& scratch);

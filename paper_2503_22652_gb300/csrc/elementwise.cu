@@ -221,6 +221,28 @@ void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out, do
   RC_LAUNCH();
 }
 
+namespace {
+// A += factor * tr(A) * I (one block: the trace, then the diagonal update)
+__global__ void shift_diag_trace_kernel(int n, double* A, int lda, double factor) {
+  __shared__ double part[256];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += A[(int64_t)i * lda + i];
+  part[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double shift = factor * part[0];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * lda + i] += shift;
+}
+}  // namespace
+
+void shift_diag_by_trace_f64(cudaStream_t s, int n, double* A, int lda, double factor) {
+  shift_diag_trace_kernel<<<1, 256, 0, s>>>(n, A, lda, factor);
+  RC_LAUNCH();
+}
+
 void fill_zero(cudaStream_t s, void* p, size_t bytes) { RC_CUDA(cudaMemsetAsync(p, 0, bytes, s)); }
 
 void scaled_copy_f64(cudaStream_t s, int64_t n, const double* in, double* out, double scale) {

@@ -15,17 +15,18 @@
 // Per (cell, column tile): D (128 x BN, FP32 in TMEM) = (A_c D_c^-1) (128 x 128: the cell matrix
 // with its columns scaled by D^-1 at the cell's dofs, padded from n_c <= 128, packed once per
 // operator as a K-major 128-byte-swizzled TF32 image) x V_c (128 x BN: the cell's rows of S_{k-1}).
-// V_c is gathered from the row-major block by TMA (tile::gather4: four rows of 32 columns per
-// copy) straight into the MN-major 128-byte-swizzled layout that the MMA reads (the 32 columns of
-// a row contiguous, 8 rows per 1024-byte atom), so no thread touches the operand: the MMA reads the
-// stored FP32 values as TF32.
+// The rows of V_c are gathered from the row-major block by TMA (tile::gather4: four rows of 32
+// columns per copy, 128-byte swizzle) into a ring of staging buffers; converter threads turn each
+// staged tile into the K-major operand (one cell node per thread: the swizzled staging reads and
+// the operand writes are both free of bank conflicts), rounding to TF32.
 //
-// Warp roles (320 threads):
+// Warp roles (448 threads):
 //   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile, lane l
-//              issues BN/32 gather4 copies of the cell's nodes 4l..4l+3 into a ring of stages;
+//              issues BN/32 gather4 copies of the cell's nodes 4l..4l+3;
 //   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), two TMEM
 //              accumulators of BN columns;
-//   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4).. (one cell node per thread) and half
+//   warps 2-5  converters: staging -> K-major TF32 operand (nimg buffers), fence.proxy.async;
+//   warps 6-13 epilogue: warp w reads TMEM lanes 32 (w % 4).. (one cell node per thread) and half
 //              of the tile's columns; it scales by alpha, adds the owner terms (the row's S_{k-1}
 //              and W values, loaded before it waits for the accumulator) and scatter-adds with
 //              red.global.add.v4.f32.
@@ -47,7 +48,7 @@ namespace rchfsi {
 namespace {
 
 constexpr int kNCP = 128;                       // padded cell size (MMA M and K)
-constexpr int kThreads = 320;                   // 10 warps
+constexpr int kThreads = 448;                   // 14 warps
 constexpr uint32_t kABytes = kNCP * kNCP * 4;   // TF32 cell image
 constexpr uint32_t kChunkBytes = kNCP * 128;    // 32 columns of V_c: 128 rows of 128 bytes
 constexpr int kMaxParts = 64;
@@ -97,7 +98,7 @@ struct StepPartDev {
 struct StepBatch {
   StepPartDev part[kMaxParts];
   int64_t total_cells;
-  int nparts, nA, nslots;
+  int nparts, nA, nslots, nimg;
   uint32_t tmem_cols;
   int* err;
 };
@@ -125,30 +126,30 @@ __device__ __forceinline__ void gather4(void* dst, const CUtensorMap* map, int x
       : "memory");
 }
 
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
-// Descriptor of an MN-major operand with 128-byte swizzle: 8 K-rows of 128 bytes per 1024-byte
-// atom (stride byte offset 1024 between atoms along K), 32-element column chunks `lbo` bytes apart
-// (leading byte offset).
-__device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t smem_addr, uint32_t lbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((smem_addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
+// Byte offset of element (row r, k) of a K-major 128-byte-swizzled FP32 operand with `rows` rows
+// per 32-element K block.
+__device__ __forceinline__ uint32_t img_off(int r, int k, int rows) {
+  const int kb = k >> 5, byte = (k & 31) * 4;
+  return (uint32_t)kb * rows * 128 + (uint32_t)r * 128 + ((((byte >> 4) ^ (r & 7))) << 4) + (byte & 15);
 }
 
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_constant__ StepBatch p) {
   constexpr int NCH = BN / 32;
-  constexpr uint32_t kSlotBytes = NCH * kChunkBytes;
-  constexpr int HB = BN / 2;  // columns of one epilogue thread per tile
+  constexpr uint32_t kSlotBytes = NCH * kChunkBytes;   // staging: 128 rows of BN FP32 values
+  constexpr uint32_t kImgBytes = BN * kNCP * 4;        // K-major operand: BN rows of 128 K values
+  constexpr int HB = BN / 2;                           // columns of one epilogue thread per tile
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[4], bempty[4], accfull[2], accempty[2], mma_done;
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[4], bempty[4], ifull[2], iempty[2], accfull[2],
+      accempty[2], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -156,17 +157,20 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)p.nA * kABytes;
+  uint8_t* sI = sB + (size_t)p.nslots * kSlotBytes;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&afull[i], 1);
       tc::mbar_init(&aempty[i], 1);
+      tc::mbar_init(&ifull[i], 128);
+      tc::mbar_init(&iempty[i], 1);
       tc::mbar_init(&accfull[i], 1);
       tc::mbar_init(&accempty[i], 256);
     }
     for (int i = 0; i < 4; ++i) {
       tc::mbar_init(&bfull[i], 1);
-      tc::mbar_init(&bempty[i], 1);
+      tc::mbar_init(&bempty[i], 128);
     }
     tc::mbar_init(&mma_done, 1);
     tc::fence_barrier_init();
@@ -186,10 +190,10 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     atomicExch(p.err, 1);
   };
   const int64_t G = gridDim.x;
-  const int nA = p.nA, nS = p.nslots;
+  const int nA = p.nA, nS = p.nslots, nI = p.nimg;
 
   if (warp == 0) {
-    // ---------------- loader
+    // ---------------- loader: cell images (bulk copies) and gathered rows of V (TMA gather4)
     int64_t j = 0, cl = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
@@ -225,7 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         }
         uint8_t* dst = sB + (size_t)s * kSlotBytes + lane * 512;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) gather4(dst + c * kChunkBytes, &P.vmap, t * BN + 32 * c, r[0], r[1], r[2], r[3], &bfull[s]);
+        for (int c = 0; c < NCH; ++c)
+          gather4(dst + c * kChunkBytes, &P.vmap, t * BN + 32 * c, r[0], r[1], r[2], r[3], &bfull[s]);
       }
     }
     if (*vabort && lane == 0) {
@@ -236,17 +241,17 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   } else if (warp == 1) {
     // ---------------- MMA issuer
     const bool leader = tc::elect_one();
-    constexpr uint32_t idesc = tc::instr_desc(2u, kNCP, BN) | (1u << 16);  // TF32, B MN-major
+    constexpr uint32_t idesc = tc::instr_desc(2u, kNCP, BN);  // TF32, both operands K-major
     int64_t j = 0, cl = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
       const StepPartDev& P = p.part[part_of(p, g)];
       const int ab = (int)(cl % nA);
       for (int t = 0; t < P.ntiles; ++t, ++j) {
-        const int s = (int)(j % nS), xb = (int)(j & 1);
+        const int ib = (int)(j % nI), xb = (int)(j & 1);
         bool ok = !*vabort;
         if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl / nA) & 1));
-        if (ok) ok = tc::mbar_wait(&bfull[s], (uint32_t)((j / nS) & 1));
+        if (ok) ok = tc::mbar_wait(&ifull[ib], (uint32_t)((j / nI) & 1));
         if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
         if (!__all_sync(0xffffffffu, ok)) {
           if (leader) fail();
@@ -255,17 +260,18 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         }
         tc::tc_fence_after();
         const uint64_t a0 = tc::sw128_desc(tc::smem_u32(sA + (size_t)ab * kABytes));
-        const uint64_t b0 = mn_sw128_desc(tc::smem_u32(sB + (size_t)s * kSlotBytes), kChunkBytes);
+        const uint64_t b0 = tc::sw128_desc(tc::smem_u32(sI + (size_t)ib * kImgBytes));
         const uint32_t d = tmem + (uint32_t)(xb * BN);
 #pragma unroll
         for (int kk = 0; kk < kNCP / 8; ++kk) {
           const int kel = kk * 8;
           const uint32_t aoff = (uint32_t)(kel >> 5) * kNCP * 128 + (uint32_t)((kel & 31) * 4);
-          if (leader) tc::mma_tf32(d, tc::desc_add(a0, aoff), tc::desc_add(b0, (uint32_t)kk * 1024u), idesc, kk > 0 ? 1u : 0u);
+          const uint32_t boff = (uint32_t)(kel >> 5) * BN * 128 + (uint32_t)((kel & 31) * 4);
+          if (leader) tc::mma_tf32(d, tc::desc_add(a0, aoff), tc::desc_add(b0, boff), idesc, kk > 0 ? 1u : 0u);
         }
         __syncwarp();
         if (leader) {
-          tc::mma_commit(&bempty[s]);
+          tc::mma_commit(&iempty[ib]);
           tc::mma_commit(&accfull[xb]);
           if (t == P.ntiles - 1) tc::mma_commit(&aempty[ab]);
         }
@@ -278,10 +284,49 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       tc::mbar_wait(&mma_done, 0u);
     }
     __syncwarp();
+  } else if (warp < 6) {
+    // ---------------- converters: thread k takes row k (cell node k) of the gathered tile and writes
+    // it, rounded to TF32, as column k of the K-major operand (BN rows of 128 K values)
+    const int k = (warp - 2) * 32 + lane;
+    int64_t j = 0, cl = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
+      const StepPartDev& P = p.part[part_of(p, g)];
+      const bool real = k < P.nc;
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int s = (int)(j % nS), ib = (int)(j % nI);
+        bool ok = !*vabort && tc::mbar_wait(&bfull[s], (uint32_t)((j / nS) & 1));
+        if (ok) ok = tc::mbar_wait(&iempty[ib], (uint32_t)((j / nI) & 1) ^ 1u);
+        if (!ok) fail();
+        if (!__all_sync(0xffffffffu, ok && !*vabort)) {
+          stop = true;
+          break;
+        }
+        const uint8_t* src = sB + (size_t)s * kSlotBytes + (size_t)k * 128;
+        uint8_t* img = sI + (size_t)ib * kImgBytes;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            // 16-byte chunk q of row k sits at chunk q ^ (k % 8) (the 128-byte swizzle of the copy)
+            float4 v = *reinterpret_cast<const float4*>(src + c * kChunkBytes + ((q ^ (k & 7)) << 4));
+            if (!real) v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int col = c * 32 + 4 * q;
+            *reinterpret_cast<float*>(img + img_off(col, k, BN)) = tf32_rna(v.x);
+            *reinterpret_cast<float*>(img + img_off(col + 1, k, BN)) = tf32_rna(v.y);
+            *reinterpret_cast<float*>(img + img_off(col + 2, k, BN)) = tf32_rna(v.z);
+            *reinterpret_cast<float*>(img + img_off(col + 3, k, BN)) = tf32_rna(v.w);
+          }
+        }
+        fence_proxy_async();  // the generic-proxy writes, before the MMA reads them
+        tc::mbar_arrive(&ifull[ib]);
+        tc::mbar_arrive(&bempty[s]);
+      }
+    }
   } else {
     // ---------------- epilogue
     const int q = warp & 3;              // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;       // column half of the tile
+    const int h = (warp - 6) >> 2;       // column half of the tile
     const int i = q * 32 + lane;         // cell-local node of this thread's accumulator row
     int64_t j = 0;
     bool stop = false;
@@ -358,21 +403,21 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   }
 }
 
-// Shared-memory plan of a tile width: cell-image buffers and stages that fit.
+// Shared-memory plan of a tile width: cell-image buffers, staging and operand stages that fit.
 struct Plan {
-  int nA, nslots;
+  int nA, nslots, nimg;
   size_t smem;
 };
 
 Plan make_plan(int BN) {
-  const size_t slot = (size_t)(BN / 32) * kChunkBytes;
+  const size_t slot = (size_t)(BN / 32) * kChunkBytes, img = (size_t)BN * kNCP * 4;
   const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
-  for (int nA : {2, 1})
-    for (int ns : {4, 3, 2}) {
-      const size_t need = (size_t)nA * kABytes + (size_t)ns * slot;
-      if (need <= cap) return Plan{nA, ns, need + 1024};
-    }
-  return Plan{0, 0, 0};
+  const int pref[][3] = {{2, 3, 2}, {1, 3, 2}, {2, 2, 2}, {2, 2, 1}, {1, 2, 2}, {1, 2, 1}};
+  for (const auto& c : pref) {
+    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * slot + (size_t)c[2] * img;
+    if (need <= cap) return Plan{c[0], c[1], c[2], need + 1024};
+  }
+  return Plan{0, 0, 0, 0};
 }
 
 CUtensorMap row_map(const float* base, int64_t rows, int n) {
@@ -443,14 +488,14 @@ int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const doub
 
 void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, int num_sms) {
   RC_CHECK(nparts >= 1 && nparts <= kMaxParts, RCHFSI_ERR_INVALID_ARG, "fused FE step: 1..64 parts per launch");
-  RC_CHECK(BN == 32 || BN == 64 || BN == 96 || BN == 128, RCHFSI_ERR_INVALID_ARG,
-           "fused FE step: column tile of 32, 64, 96 or 128");
+  RC_CHECK(BN == 32 || BN == 64 || BN == 96, RCHFSI_ERR_INVALID_ARG, "fused FE step: column tile of 32, 64 or 96");
   const Plan pl = make_plan(BN);
   RC_CHECK(pl.nA > 0, RCHFSI_ERR_INVALID_ARG, "fused FE step: no shared-memory plan for this tile");
   StepBatch b{};
   b.nparts = nparts;
   b.nA = pl.nA;
   b.nslots = pl.nslots;
+  b.nimg = pl.nimg;
   int64_t off = 0;
   double flops = 0.0, bytes = 0.0;
   for (int q = 0; q < nparts; ++q) {
@@ -495,8 +540,7 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
   switch (BN) {
     case 32: launch<32>(s, b, pl, grid); break;
     case 64: launch<64>(s, b, pl, grid); break;
-    case 96: launch<96>(s, b, pl, grid); break;
-    default: launch<128>(s, b, pl, grid); break;
+    default: launch<96>(s, b, pl, grid); break;
   }
 }
 
@@ -508,7 +552,7 @@ int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, c
     if (it != g_tune.end()) return it->second;
   }
   std::vector<int> cand;
-  for (int bn : {32, 64, 96, 128})
+  for (int bn : {32, 64, 96})
     if (bn <= std::max(32, (n + 31) / 32 * 32)) cand.push_back(bn);
   DevBuf<float> scratch;
   float* out = scratch.ensure((size_t)op.m * n);

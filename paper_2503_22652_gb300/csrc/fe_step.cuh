@@ -35,7 +35,7 @@ int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const doub
 // Pack the operator's scaled cell images (A_c D_c^-1, TF32) and owner masks ahead of a capture.
 void fe_step_prepare(cudaStream_t s, FeOp& op);
 
-// All parts (at most 64) in one persistent launch; BN = column tile (32, 64, 96 or 128).
+// All parts (at most 64) in one persistent launch; BN = column tile (32, 64 or 96).
 void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, int num_sms);
 
 // Column tile for this operator and width, chosen by timing the candidates once per shape on the

@@ -79,6 +79,7 @@ struct rchfsi_ctx {
   rchfsi::DevBuf<int> ccols;      // embedded columns selected for complex outputs
   rchfsi::DevBuf<double> cdot;    // complex inner product scratch
   bool rr_paired = false;         // the last Rayleigh-Ritz already kept one Ritz vector per complex pair
+  int rr_retries = 0;             // the last Rayleigh-Ritz needed the shifted Cholesky QR step
   rchfsi::prof::Profiler prof;
 };
 

@@ -79,3 +79,27 @@ def test_chfsi_with_inexact_inverse_stagnates():
     _, _, _, st3 = s.solve(wl.gaussian_block(m, N, seed=2), allow_not_converged=True)
     assert st3["status"] in (_lib.OK, _lib.ERR_NOT_CONVERGED)
     assert st3["max_rel_residual"] < 1e-2 * st["max_rel_residual"]
+
+
+def test_nearly_dependent_block_goes_through_shifted_cholesky_qr():
+    """A Gaussian initial block with eight pairs of columns that agree to 1e-10: the Gram matrix of
+    the first Rayleigh-Ritz step has no Cholesky factor in FP64, so the basis is preconditioned by
+    one shifted Cholesky QR step (B inner product) and the solve proceeds to the prescribed
+    eigenvalues.  The rounding that decides whether a pivot of a near-singular Gram matrix comes out
+    positive varies with the data, so several seeded blocks are tried and at least one must take
+    the retry."""
+    m, N, nev = 300, 24, 10
+    c = wl.dense_config1(m=m)
+    retried = 0
+    for seed in (3, 4, 5):
+        X0 = wl.gaussian_block(m, N, seed=seed)
+        rng = np.random.default_rng(seed)
+        for j in range(0, 16, 2):
+            X0[:, j + 1] = X0[:, j] + 1e-10 * rng.standard_normal(m)
+        s = Solver(m, nev=nev, block=N, degree=12, max_iter=100)
+        s.set_dense(c["A"])
+        X, ev, res, st = s.solve(X0)
+        assert st["status"] == _lib.OK and st["max_rel_residual"] <= 1e-8
+        np.testing.assert_allclose(ev[:nev], c["lam"][:nev], atol=1e-9 * 11.0)
+        retried += st["cholqr_retries"] > 0
+    assert retried >= 1
