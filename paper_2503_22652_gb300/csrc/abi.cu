@@ -374,17 +374,27 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
     RC_CHECK(hd[i] >= 0 && hd[i] < mc, RCHFSI_ERR_INVALID_ARG, "cell_dofs entry out of [0, m)");
   // owner of each dof: the first cell (in cell order) that contains it
   {
-    std::vector<uint32_t> own((size_t)f.n_cells * 4, 0u);
+    const size_t C = (size_t)f.n_cells;
+    std::vector<int> rows(C * 128, 0), cnt(C, 0);
+    std::vector<int8_t> pos(C * 128, -1);
     std::vector<uint8_t> seen((size_t)mc, 0);
-    for (int64_t cl = 0; cl < f.n_cells; ++cl)
+    for (size_t cl = 0; cl < C; ++cl) {
+      int n = 0;
       for (int k = 0; k < f.nc; ++k) {
-        const int d = hd[(size_t)cl * f.nc + k];
+        const int d = hd[cl * f.nc + k];
         if (!seen[d]) {
           seen[d] = 1;
-          own[(size_t)cl * 4 + (k >> 5)] |= 1u << (k & 31);
+          pos[cl * 128 + k] = (int8_t)n;
+          rows[cl * 128 + n++] = d;
         }
       }
-    RC_CUDA(cudaMemcpyAsync(f.own.ensure(own.size()), own.data(), own.size() * sizeof(uint32_t),
+      cnt[cl] = n;
+      for (int k = n; k < 128; ++k) rows[cl * 128 + k] = n ? rows[cl * 128 + n - 1] : hd[cl * f.nc];
+    }
+    RC_CUDA(cudaMemcpyAsync(f.own_rows.ensure(rows.size()), rows.data(), rows.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(f.own_pos.ensure(pos.size()), pos.data(), pos.size(), cudaMemcpyHostToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(f.own_cnt.ensure(cnt.size()), cnt.data(), cnt.size() * sizeof(int),
                             cudaMemcpyHostToDevice, c.s));
     RC_CUDA(cudaStreamSynchronize(c.s));
   }
@@ -409,7 +419,10 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
     to_device(c, op->A_cells, tmp.ensure(2 * na), 2 * na);
     cplx_deinterleave(c.s, na, tmp.p, f.A64.ensure(na), g.A64.ensure(na));
     RC_CUDA(cudaMemcpyAsync(g.dofs.ensure(nd), dofs, nd * sizeof(int), cudaMemcpyDeviceToDevice, c.s));
-    RC_CUDA(cudaMemcpyAsync(g.own.ensure(f.own.n), f.own.p, f.own.bytes(), cudaMemcpyDeviceToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(g.own_rows.ensure(f.own_rows.n), f.own_rows.p, f.own_rows.bytes(), cudaMemcpyDeviceToDevice,
+                            c.s));
+    RC_CUDA(cudaMemcpyAsync(g.own_pos.ensure(f.own_pos.n), f.own_pos.p, f.own_pos.bytes(), cudaMemcpyDeviceToDevice, c.s));
+    RC_CUDA(cudaMemcpyAsync(g.own_cnt.ensure(f.own_cnt.n), f.own_cnt.p, f.own_cnt.bytes(), cudaMemcpyDeviceToDevice, c.s));
     // D^-1 of the embedding: [D^-1; D^-1]
     double* dv = f.Dinv.ensure(2 * mc);
     to_device(c, op->Dinv, dv, mc);

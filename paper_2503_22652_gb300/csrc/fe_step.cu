@@ -12,24 +12,25 @@
 // then read once and S_k written once per step, the four block streams of the algorithm, plus
 // the cell matrices.
 //
-// Per (cell, column tile): D (128 x BN, FP32 in TMEM) = (A_c D_c^-1) (128 x 128: the cell matrix
-// with its columns scaled by D^-1 at the cell's dofs, padded from n_c <= 128, packed once per
-// operator as a K-major 128-byte-swizzled TF32 image) x V_c (128 x BN: the cell's rows of S_{k-1}).
-// The rows of V_c are gathered from the row-major block by TMA (tile::gather4: four rows of 32
-// columns per copy, 128-byte swizzle) into a ring of staging buffers; converter threads turn each
-// staged tile into the K-major operand (one cell node per thread: the swizzled staging reads and
-// the operand writes are both free of bank conflicts), rounding to TF32.
+// Per (cell, column tile): D (128 x BN, FP32 in TMEM) = T + (A_c D_c^-1) V_c, where A_c D_c^-1 is the
+// cell matrix with its columns scaled by D^-1 at the cell's dofs (padded from n_c <= 128 to 128 x
+// 128, packed once per operator as a K-major 128-byte-swizzled TF32 image), V_c (128 x BN) the
+// cell's rows of S_{k-1}, and T the owner terms of the cell's owned rows divided by alpha, so that
+// alpha D is the whole contribution of the cell.  The rows of V_c and the owned rows of W are
+// gathered from the row-major blocks by TMA (tile::gather4: four rows of 32 columns per copy,
+// 128-byte swizzle) into a ring of stages.  Converter threads (one cell node each) read their
+// rows, store T into the accumulator with tcgen05.st, and, after a barrier among themselves,
+// rewrite the stage in place as the K-major TF32 operand of the MMA (the swizzled reads and the
+// operand writes are both free of shared-memory bank conflicts).
 //
-// Warp roles (448 threads):
+// Warp roles (320 threads):
 //   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile, lane l
-//              issues BN/32 gather4 copies of the cell's nodes 4l..4l+3;
-//   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), two TMEM
-//              accumulators of BN columns;
-//   warps 2-5  converters: staging -> K-major TF32 operand (nimg buffers), fence.proxy.async;
-//   warps 6-13 epilogue: warp w reads TMEM lanes 32 (w % 4).. (one cell node per thread) and half
-//              of the tile's columns; it scales by alpha, adds the owner terms (the row's S_{k-1}
-//              and W values, loaded before it waits for the accumulator) and scatter-adds with
-//              red.global.add.v4.f32.
+//              gathers the cell's nodes 4l..4l+3 of V and owned rows 4l..4l+3 of W;
+//   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), accumulating
+//              onto the owner terms in one of two TMEM accumulators of BN columns;
+//   warps 2-5  converters (warp w: nodes 32 (w % 4).., the TMEM lanes it may access);
+//   warps 6-9  epilogue: TMEM lanes 32 (w % 4).. (one cell node per thread); alpha scaling and
+//              red.global.add.v4.f32 into the output rows.
 // Every mbarrier wait is bounded; on a timeout the kernel raises the error flag, waits (bounded)
 // for its copies and MMAs in flight, releases TMEM and returns.
 #include <cudaTypedefs.h>
@@ -48,7 +49,7 @@ namespace rchfsi {
 namespace {
 
 constexpr int kNCP = 128;                       // padded cell size (MMA M and K)
-constexpr int kThreads = 448;                   // 14 warps
+constexpr int kThreads = 320;                   // 10 warps
 constexpr uint32_t kABytes = kNCP * kNCP * 4;   // TF32 cell image
 constexpr uint32_t kChunkBytes = kNCP * 128;    // 32 columns of V_c: 128 rows of 128 bytes
 constexpr int kMaxParts = 64;
@@ -82,8 +83,12 @@ __global__ void pack_scaled_kernel(int64_t n_cells, int nc, const double* __rest
 
 struct StepPartDev {
   CUtensorMap vmap;       // rows of V: 2D {n, rows}, box {32, 1}, 128-byte swizzle, zero fill
+  CUtensorMap wmap;       // rows of W, same form
   const int* dofs;
-  const uint32_t* own;    // 4 words per cell (bit i: the cell owns its node i); null: no owner terms
+  const int* own_rows;    // per cell 128 entries: the dofs the cell owns, in node order, padded by
+                          // repeating the last one (null: no owner terms in this part)
+  const int8_t* own_pos;  // per cell 128 entries: position of node k in own_rows, -1 if not owned
+  const int* own_cnt;     // per cell: number of owned nodes
   const uint8_t* img;
   const float* V;
   const float* W;
@@ -98,7 +103,7 @@ struct StepPartDev {
 struct StepBatch {
   StepPartDev part[kMaxParts];
   int64_t total_cells;
-  int nparts, nA, nslots, nimg;
+  int nparts, nA, nslots;
   uint32_t tmem_cols;
   int* err;
 };
@@ -144,12 +149,11 @@ __device__ __forceinline__ uint32_t img_off(int r, int k, int rows) {
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_constant__ StepBatch p) {
   constexpr int NCH = BN / 32;
-  constexpr uint32_t kSlotBytes = NCH * kChunkBytes;   // staging: 128 rows of BN FP32 values
-  constexpr uint32_t kImgBytes = BN * kNCP * 4;        // K-major operand: BN rows of 128 K values
-  constexpr int HB = BN / 2;                           // columns of one epilogue thread per tile
+  constexpr uint32_t kHalf = NCH * kChunkBytes;   // 128 rows of BN FP32 values
+  constexpr uint32_t kSlotBytes = 2 * kHalf;      // V rows (then the operand), owned W rows
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[4], bempty[4], ifull[2], iempty[2], accfull[2],
-      accempty[2], mma_done;
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[4], bempty[4], ifull[4], accfull[2], accempty[2],
+      cvt_read, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -157,21 +161,20 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)p.nA * kABytes;
-  uint8_t* sI = sB + (size_t)p.nslots * kSlotBytes;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&afull[i], 1);
       tc::mbar_init(&aempty[i], 1);
-      tc::mbar_init(&ifull[i], 128);
-      tc::mbar_init(&iempty[i], 1);
       tc::mbar_init(&accfull[i], 1);
-      tc::mbar_init(&accempty[i], 256);
+      tc::mbar_init(&accempty[i], 128);
     }
     for (int i = 0; i < 4; ++i) {
       tc::mbar_init(&bfull[i], 1);
-      tc::mbar_init(&bempty[i], 128);
+      tc::mbar_init(&bempty[i], 1);
+      tc::mbar_init(&ifull[i], 128);
     }
+    tc::mbar_init(&cvt_read, 128);
     tc::mbar_init(&mma_done, 1);
     tc::fence_barrier_init();
     abort_flag = 0;
@@ -190,18 +193,23 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     atomicExch(p.err, 1);
   };
   const int64_t G = gridDim.x;
-  const int nA = p.nA, nS = p.nslots, nI = p.nimg;
+  const int nA = p.nA, nS = p.nslots;
 
   if (warp == 0) {
-    // ---------------- loader: cell images (bulk copies) and gathered rows of V (TMA gather4)
+    // ---------------- loader: cell images (bulk copies), gathered rows of V and owned rows of W
     int64_t j = 0, cl = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
       const StepPartDev& P = p.part[part_of(p, g)];
       const int64_t cell = g - P.cell_off;
-      int r[4];
+      int r[4], w[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) r[u] = __ldg(P.dofs + cell * P.nc + min(4 * lane + u, P.nc - 1));
+      const int cnt = P.own_rows ? __ldg(P.own_cnt + cell) : 0;
+      const bool wl = 4 * lane < cnt;  // this lane gathers owned rows 4l..4l+3 of W
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[u] = wl ? __ldg(P.own_rows + cell * kNCP + 4 * lane + u) : 0;
+      const uint32_t tile_bytes = kHalf + (uint32_t)((cnt + 3) / 4) * NCH * 512u;
       const int ab = (int)(cl % nA);
       int ok = 1;
       if (lane == 0) {
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         const int s = (int)(j % nS);
         if (lane == 0) {
           ok = !*vabort && tc::mbar_wait(&bempty[s], (uint32_t)((j / nS) & 1) ^ 1u);
-          if (ok) tc::mbar_arrive_expect_tx(&bfull[s], kSlotBytes);
+          if (ok) tc::mbar_arrive_expect_tx(&bfull[s], tile_bytes);
         }
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
           if (lane == 0) fail();
@@ -229,8 +237,10 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         }
         uint8_t* dst = sB + (size_t)s * kSlotBytes + lane * 512;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c)
+        for (int c = 0; c < NCH; ++c) {
           gather4(dst + c * kChunkBytes, &P.vmap, t * BN + 32 * c, r[0], r[1], r[2], r[3], &bfull[s]);
+          if (wl) gather4(dst + kHalf + c * kChunkBytes, &P.wmap, t * BN + 32 * c, w[0], w[1], w[2], w[3], &bfull[s]);
+        }
       }
     }
     if (*vabort && lane == 0) {
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       for (int64_t j2 = (j > nS ? j - nS : 0); j2 < j; ++j2) tc::mbar_wait(&bfull[j2 % nS], (uint32_t)((j2 / nS) & 1));
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: accumulates onto the owner terms the converters stored
     const bool leader = tc::elect_one();
     constexpr uint32_t idesc = tc::instr_desc(2u, kNCP, BN);  // TF32, both operands K-major
     int64_t j = 0, cl = 0;
@@ -248,11 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       const StepPartDev& P = p.part[part_of(p, g)];
       const int ab = (int)(cl % nA);
       for (int t = 0; t < P.ntiles; ++t, ++j) {
-        const int ib = (int)(j % nI), xb = (int)(j & 1);
+        const int s = (int)(j % nS), xb = (int)(j & 1);
         bool ok = !*vabort;
         if (ok && t == 0) ok = tc::mbar_wait(&afull[ab], (uint32_t)((cl / nA) & 1));
-        if (ok) ok = tc::mbar_wait(&ifull[ib], (uint32_t)((j / nI) & 1));
-        if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
+        if (ok) ok = tc::mbar_wait(&ifull[s], (uint32_t)((j / nS) & 1));
         if (!__all_sync(0xffffffffu, ok)) {
           if (leader) fail();
           stop = true;
@@ -260,18 +269,18 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         }
         tc::tc_fence_after();
         const uint64_t a0 = tc::sw128_desc(tc::smem_u32(sA + (size_t)ab * kABytes));
-        const uint64_t b0 = tc::sw128_desc(tc::smem_u32(sI + (size_t)ib * kImgBytes));
+        const uint64_t b0 = tc::sw128_desc(tc::smem_u32(sB + (size_t)s * kSlotBytes));
         const uint32_t d = tmem + (uint32_t)(xb * BN);
 #pragma unroll
         for (int kk = 0; kk < kNCP / 8; ++kk) {
           const int kel = kk * 8;
           const uint32_t aoff = (uint32_t)(kel >> 5) * kNCP * 128 + (uint32_t)((kel & 31) * 4);
           const uint32_t boff = (uint32_t)(kel >> 5) * BN * 128 + (uint32_t)((kel & 31) * 4);
-          if (leader) tc::mma_tf32(d, tc::desc_add(a0, aoff), tc::desc_add(b0, boff), idesc, kk > 0 ? 1u : 0u);
+          if (leader) tc::mma_tf32(d, tc::desc_add(a0, aoff), tc::desc_add(b0, boff), idesc, 1u);
         }
         __syncwarp();
         if (leader) {
-          tc::mma_commit(&iempty[ib]);
+          tc::mma_commit(&bempty[s]);
           tc::mma_commit(&accfull[xb]);
           if (t == P.ntiles - 1) tc::mma_commit(&aempty[ab]);
         }
@@ -285,54 +294,15 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     }
     __syncwarp();
   } else if (warp < 6) {
-    // ---------------- converters: thread k takes row k (cell node k) of the gathered tile and writes
-    // it, rounded to TF32, as column k of the K-major operand (BN rows of 128 K values)
-    const int k = (warp - 2) * 32 + lane;
-    int64_t j = 0, cl = 0;
-    bool stop = false;
-    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
-      const StepPartDev& P = p.part[part_of(p, g)];
-      const bool real = k < P.nc;
-      for (int t = 0; t < P.ntiles; ++t, ++j) {
-        const int s = (int)(j % nS), ib = (int)(j % nI);
-        bool ok = !*vabort && tc::mbar_wait(&bfull[s], (uint32_t)((j / nS) & 1));
-        if (ok) ok = tc::mbar_wait(&iempty[ib], (uint32_t)((j / nI) & 1) ^ 1u);
-        if (!ok) fail();
-        if (!__all_sync(0xffffffffu, ok && !*vabort)) {
-          stop = true;
-          break;
-        }
-        const uint8_t* src = sB + (size_t)s * kSlotBytes + (size_t)k * 128;
-        uint8_t* img = sI + (size_t)ib * kImgBytes;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            // 16-byte chunk q of row k sits at chunk q ^ (k % 8) (the 128-byte swizzle of the copy)
-            float4 v = *reinterpret_cast<const float4*>(src + c * kChunkBytes + ((q ^ (k & 7)) << 4));
-            if (!real) v = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int col = c * 32 + 4 * q;
-            *reinterpret_cast<float*>(img + img_off(col, k, BN)) = tf32_rna(v.x);
-            *reinterpret_cast<float*>(img + img_off(col + 1, k, BN)) = tf32_rna(v.y);
-            *reinterpret_cast<float*>(img + img_off(col + 2, k, BN)) = tf32_rna(v.z);
-            *reinterpret_cast<float*>(img + img_off(col + 3, k, BN)) = tf32_rna(v.w);
-          }
-        }
-        fence_proxy_async();  // the generic-proxy writes, before the MMA reads them
-        tc::mbar_arrive(&ifull[ib]);
-        tc::mbar_arrive(&bempty[s]);
-      }
-    }
-  } else {
-    // ---------------- epilogue
-    const int q = warp & 3;              // TMEM lane quarter this warp may access
-    const int h = (warp - 6) >> 2;       // column half of the tile
-    const int i = q * 32 + lane;         // cell-local node of this thread's accumulator row
+    // ---------------- converters: thread k owns cell node k (and TMEM lane k)
+    const int k = (warp & 3) * 32 + lane;
     int64_t j = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
       const StepPartDev& P = p.part[part_of(p, g)];
       const int64_t cell = g - P.cell_off;
+      const bool real = k < P.nc;
+      const int o = (real && P.own_rows) ? (int)__ldg(P.own_pos + cell * kNCP + k) : -1;
       float al = P.alpha, be = P.beta, om = P.omega;
       if (P.coef) {
         al = (float)__ldg(P.coef);
@@ -340,27 +310,94 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         om = (float)__ldg(P.coef + 2);
       }
       al *= P.sign;
-      int64_t row = -1;
-      bool own = false;
-      if (i < P.nc) {
-        row = (int64_t)__ldg(P.dofs + cell * P.nc + i) * P.n;
-        own = P.own && ((__ldg(P.own + cell * 4 + (i >> 5)) >> (i & 31)) & 1u);
-      }
+      const float rbe = be / al, rom = om / al;  // owner terms divided by alpha
       for (int t = 0; t < P.ntiles; ++t, ++j) {
-        const int xb = (int)(j & 1);
-        const int c0 = t * BN + h * HB;
-        // owner terms: this row's S_{k-1} and W values, in flight while the MMA finishes
-        float4 vv[HB / 4], ww[HB / 4];
-        if (own) {
+        const int s = (int)(j % nS), xb = (int)(j & 1);
+        bool ok = !*vabort && tc::mbar_wait(&bfull[s], (uint32_t)((j / nS) & 1));
+        if (ok) ok = tc::mbar_wait(&accempty[xb], (uint32_t)((j >> 1) & 1) ^ 1u);
+        if (!ok) fail();
+        if (!__all_sync(0xffffffffu, ok && !*vabort)) {
+          stop = true;
+          break;
+        }
+        tc::tc_fence_after();
+        uint8_t* slot = sB + (size_t)s * kSlotBytes;
+        const uint8_t* vrow = slot + (size_t)k * 128;
+        const uint8_t* wrow = slot + kHalf + (size_t)(o < 0 ? 0 : o) * 128;
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(xb * BN);
+        float4 v[BN / 4];
 #pragma unroll
-          for (int u = 0; u < HB / 4; ++u) {
-            const int col = c0 + 4 * u;
-            if (col < P.n) {
-              vv[u] = __ldg(reinterpret_cast<const float4*>(P.V + row + col));
-              ww[u] = __ldg(reinterpret_cast<const float4*>(P.W + row + col));
+        for (int c = 0; c < NCH; ++c) {
+          float tv[32];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            // 16-byte chunk q of a staged row r sits at chunk q ^ (r % 8) (the 128-byte swizzle)
+            float4 x = *reinterpret_cast<const float4*>(vrow + c * kChunkBytes + ((q ^ (k & 7)) << 4));
+            if (!real) x = make_float4(0.f, 0.f, 0.f, 0.f);
+            v[c * 8 + q] = x;
+            float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (o >= 0) {
+              const float4 wv = *reinterpret_cast<const float4*>(wrow + c * kChunkBytes + ((q ^ (o & 7)) << 4));
+              const int col = t * BN + c * 32 + 4 * q;
+              if (col < P.n) {
+                const double2 l01 = __ldg(reinterpret_cast<const double2*>(P.lam + col));
+                const double2 l23 = __ldg(reinterpret_cast<const double2*>(P.lam + col + 2));
+                tq.x = rbe * x.x + rom * (float)l01.x * wv.x;
+                tq.y = rbe * x.y + rom * (float)l01.y * wv.y;
+                tq.z = rbe * x.z + rom * (float)l23.x * wv.z;
+                tq.w = rbe * x.w + rom * (float)l23.y * wv.w;
+              }
             }
+            tv[4 * q] = tq.x;
+            tv[4 * q + 1] = tq.y;
+            tv[4 * q + 2] = tq.z;
+            tv[4 * q + 3] = tq.w;
+          }
+          tc::tmem_st16(taddr + c * 32, tv);
+          tc::tmem_st16(taddr + c * 32 + 16, tv + 16);
+        }
+        tc::tmem_wait_st();
+        // once every converter has read its row of the stage (a bounded wait on a barrier that
+        // completes one phase per tile), rewrite the stage as the K-major operand
+        tc::mbar_arrive(&cvt_read);
+        ok = tc::mbar_wait(&cvt_read, (uint32_t)(j & 1));
+        if (!ok) fail();
+        if (!__all_sync(0xffffffffu, ok && !*vabort)) {
+          stop = true;
+          break;
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int col = c * 32 + 4 * q;
+            const float4 x = v[c * 8 + q];
+            *reinterpret_cast<float*>(slot + img_off(col, k, BN)) = tf32_rna(x.x);
+            *reinterpret_cast<float*>(slot + img_off(col + 1, k, BN)) = tf32_rna(x.y);
+            *reinterpret_cast<float*>(slot + img_off(col + 2, k, BN)) = tf32_rna(x.z);
+            *reinterpret_cast<float*>(slot + img_off(col + 3, k, BN)) = tf32_rna(x.w);
           }
         }
+        fence_proxy_async();  // the generic-proxy writes, before the MMA reads them
+        tc::tc_fence_before();
+        tc::mbar_arrive(&ifull[s]);
+      }
+    }
+  } else {
+    // ---------------- epilogue
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int i = q * 32 + lane;         // cell-local node of this thread's accumulator row
+    int64_t j = 0;
+    bool stop = false;
+    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
+      const StepPartDev& P = p.part[part_of(p, g)];
+      const int64_t cell = g - P.cell_off;
+      float al = P.coef ? (float)__ldg(P.coef) : P.alpha;
+      al *= P.sign;
+      const int64_t row = (i < P.nc) ? (int64_t)__ldg(P.dofs + cell * P.nc + i) * P.n : -1;
+      for (int t = 0; t < P.ntiles; ++t, ++j) {
+        const int xb = (int)(j & 1);
+        const int c0 = t * BN;
         bool ok = !*vabort && tc::mbar_wait(&accfull[xb], (uint32_t)((j >> 1) & 1));
         if (!ok) fail();
         if (!__all_sync(0xffffffffu, ok && !*vabort)) {
@@ -368,26 +405,17 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
           break;
         }
         tc::tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * BN + h * HB);
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * BN);
 #pragma unroll
-        for (int cc = 0; cc < HB; cc += 16) {
+        for (int cc = 0; cc < BN; cc += 16) {
           float v[16];
           tc::tmem_ld16(taddr + cc, v);
           if (row >= 0) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int col = c0 + cc + 4 * u;
-              if (col < P.n) {
-                float o0 = al * v[4 * u], o1 = al * v[4 * u + 1], o2 = al * v[4 * u + 2], o3 = al * v[4 * u + 3];
-                if (own) {
-                  const float4 x = vv[(cc >> 2) + u], w = ww[(cc >> 2) + u];
-                  o0 += be * x.x + om * (float)__ldg(P.lam + col) * w.x;
-                  o1 += be * x.y + om * (float)__ldg(P.lam + col + 1) * w.y;
-                  o2 += be * x.z + om * (float)__ldg(P.lam + col + 2) * w.z;
-                  o3 += be * x.w + om * (float)__ldg(P.lam + col + 3) * w.w;
-                }
-                red_add_v4(P.U + row + col, o0, o1, o2, o3);
-              }
+              if (col < P.n)
+                red_add_v4(P.U + row + col, al * v[4 * u], al * v[4 * u + 1], al * v[4 * u + 2], al * v[4 * u + 3]);
             }
           }
         }
@@ -403,21 +431,21 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   }
 }
 
-// Shared-memory plan of a tile width: cell-image buffers, staging and operand stages that fit.
+// Shared-memory plan of a tile width: cell-image buffers and stages (V rows, owned W rows) that fit.
 struct Plan {
-  int nA, nslots, nimg;
+  int nA, nslots;
   size_t smem;
 };
 
 Plan make_plan(int BN) {
-  const size_t slot = (size_t)(BN / 32) * kChunkBytes, img = (size_t)BN * kNCP * 4;
+  const size_t slot = 2 * (size_t)(BN / 32) * kChunkBytes;
   const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
-  const int pref[][3] = {{2, 3, 2}, {1, 3, 2}, {2, 2, 2}, {2, 2, 1}, {1, 2, 2}, {1, 2, 1}};
+  const int pref[][2] = {{2, 4}, {2, 3}, {1, 4}, {1, 3}, {2, 2}, {1, 2}};
   for (const auto& c : pref) {
-    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * slot + (size_t)c[2] * img;
-    if (need <= cap) return Plan{c[0], c[1], c[2], need + 1024};
+    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * slot;
+    if (need <= cap) return Plan{c[0], c[1], need + 1024};
   }
-  return Plan{0, 0, 0, 0};
+  return Plan{0, 0, 0};
 }
 
 CUtensorMap row_map(const float* base, int64_t rows, int n) {
@@ -460,7 +488,7 @@ std::map<std::tuple<int, int64_t, int, int>, int> g_tune;
 }  // namespace
 
 bool fe_step_supported(const FeOp& op, int n, int precision) {
-  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own.p != nullptr;
+  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own_rows.p != nullptr;
 }
 
 void fe_step_prepare(cudaStream_t s, FeOp& op) {
@@ -495,18 +523,20 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
   b.nparts = nparts;
   b.nA = pl.nA;
   b.nslots = pl.nslots;
-  b.nimg = pl.nimg;
   int64_t off = 0;
   double flops = 0.0, bytes = 0.0;
   for (int q = 0; q < nparts; ++q) {
     const FeStepPart& t = parts[q];
     FeOp& op = *t.op;
-    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own.p, RCHFSI_ERR_INVALID_ARG,
-             "fused FE step: n_c <= 128, n a multiple of 4 and owner masks required");
+    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own_rows.p, RCHFSI_ERR_INVALID_ARG,
+             "fused FE step: n_c <= 128, n a multiple of 4 and owner lists required");
     StepPartDev& P = b.part[q];
     P.vmap = row_map(t.V, t.rows, t.n);
+    P.wmap = row_map(t.W, t.rows, t.n);
     P.dofs = op.dofs.p;
-    P.own = t.owner ? op.own.p : nullptr;
+    P.own_rows = t.owner ? op.own_rows.p : nullptr;
+    P.own_pos = op.own_pos.p;
+    P.own_cnt = op.own_cnt.p;
     // the scaled images use the D^-1 of the rows the part reads (both halves share it)
     P.img = scaled_images(s, op, op.Dinv.p);
     P.V = t.V;
