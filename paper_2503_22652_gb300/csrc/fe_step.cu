@@ -583,7 +583,7 @@ int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, c
   }
   std::vector<int> cand;
   for (int bn : {32, 64, 96})
-    if (bn <= std::max(32, (n + 31) / 32 * 32)) cand.push_back(bn);
+    if (bn <= std::max(32, (n + 31) / 32 * 32) && make_plan(bn).nA > 0) cand.push_back(bn);
   DevBuf<float> scratch;
   float* out = scratch.ensure((size_t)op.m * n);
   cudaEvent_t e0, e1;
