@@ -23,13 +23,14 @@
 // rewrite the stage in place as the K-major TF32 operand of the MMA (the swizzled reads and the
 // operand writes are both free of shared-memory bank conflicts).
 //
-// Warp roles (320 threads):
+// Warp roles (448 threads):
 //   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile, lane l
 //              gathers the cell's nodes 4l..4l+3 of V and owned rows 4l..4l+3 of W;
 //   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), accumulating
 //              onto the owner terms in one of two TMEM accumulators of BN columns;
-//   warps 2-5  converters (warp w: nodes 32 (w % 4).., the TMEM lanes it may access);
-//   warps 6-9  epilogue: TMEM lanes 32 (w % 4).. (one cell node per thread); alpha scaling and
+//   warps 2-9  converters (warp w: nodes 32 (w % 4).., the TMEM lanes it may access, and half of
+//              the tile's columns);
+//   warps 10-13 epilogue: TMEM lanes 32 (w % 4).. (one cell node per thread); alpha scaling and
 //              red.global.add.v4.f32 into the output rows.
 // Every mbarrier wait is bounded; on a timeout the kernel raises the error flag, waits (bounded)
 // for its copies and MMAs in flight, releases TMEM and returns.
@@ -49,7 +50,7 @@ namespace rchfsi {
 namespace {
 
 constexpr int kNCP = 128;                       // padded cell size (MMA M and K)
-constexpr int kThreads = 320;                   // 10 warps
+constexpr int kThreads = 448;                   // 14 warps
 constexpr uint32_t kABytes = kNCP * kNCP * 4;   // TF32 cell image
 constexpr uint32_t kChunkBytes = kNCP * 128;    // 32 columns of V_c: 128 rows of 128 bytes
 constexpr int kMaxParts = 64;
@@ -172,9 +173,9 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     for (int i = 0; i < 4; ++i) {
       tc::mbar_init(&bfull[i], 1);
       tc::mbar_init(&bempty[i], 1);
-      tc::mbar_init(&ifull[i], 128);
+      tc::mbar_init(&ifull[i], 256);
     }
-    tc::mbar_init(&cvt_read, 128);
+    tc::mbar_init(&cvt_read, 256);
     tc::mbar_init(&mma_done, 1);
     tc::fence_barrier_init();
     abort_flag = 0;
@@ -293,9 +294,12 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       tc::mbar_wait(&mma_done, 0u);
     }
     __syncwarp();
-  } else if (warp < 6) {
-    // ---------------- converters: thread k owns cell node k (and TMEM lane k)
+  } else if (warp < 10) {
+    // ---------------- converters: thread (k, h) owns cell node k (and TMEM lane k) and half h of
+    // the tile's columns
+    constexpr int HB = BN / 2;
     const int k = (warp & 3) * 32 + lane;
+    const int h = (warp - 2) >> 2;
     int64_t j = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
@@ -324,40 +328,39 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         uint8_t* slot = sB + (size_t)s * kSlotBytes;
         const uint8_t* vrow = slot + (size_t)k * 128;
         const uint8_t* wrow = slot + kHalf + (size_t)(o < 0 ? 0 : o) * 128;
-        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(xb * BN);
-        float4 v[BN / 4];
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(xb * BN + h * HB);
+        float4 v[HB / 4];
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          float tv[32];
+        for (int c16 = 0; c16 < HB / 16; ++c16) {
+          float tv[16];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            // 16-byte chunk q of a staged row r sits at chunk q ^ (r % 8) (the 128-byte swizzle)
-            float4 x = *reinterpret_cast<const float4*>(vrow + c * kChunkBytes + ((q ^ (k & 7)) << 4));
+          for (int u = 0; u < 4; ++u) {
+            const int col = h * HB + c16 * 16 + 4 * u;      // column within the tile
+            const int c = col >> 5, qd = (col & 31) >> 2;  // 32-column chunk, 16-byte chunk in the row
+            // 16-byte chunk qd of a staged row r sits at chunk qd ^ (r % 8) (the 128-byte swizzle)
+            float4 x = *reinterpret_cast<const float4*>(vrow + c * kChunkBytes + ((qd ^ (k & 7)) << 4));
             if (!real) x = make_float4(0.f, 0.f, 0.f, 0.f);
-            v[c * 8 + q] = x;
+            v[c16 * 4 + u] = x;
             float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (o >= 0) {
-              const float4 wv = *reinterpret_cast<const float4*>(wrow + c * kChunkBytes + ((q ^ (o & 7)) << 4));
-              const int col = t * BN + c * 32 + 4 * q;
-              if (col < P.n) {
-                const double2 l01 = __ldg(reinterpret_cast<const double2*>(P.lam + col));
-                const double2 l23 = __ldg(reinterpret_cast<const double2*>(P.lam + col + 2));
-                tq.x = rbe * x.x + rom * (float)l01.x * wv.x;
-                tq.y = rbe * x.y + rom * (float)l01.y * wv.y;
-                tq.z = rbe * x.z + rom * (float)l23.x * wv.z;
-                tq.w = rbe * x.w + rom * (float)l23.y * wv.w;
-              }
+            const int gcol = t * BN + col;
+            if (o >= 0 && gcol < P.n) {
+              const float4 wv = *reinterpret_cast<const float4*>(wrow + c * kChunkBytes + ((qd ^ (o & 7)) << 4));
+              const double2 l01 = __ldg(reinterpret_cast<const double2*>(P.lam + gcol));
+              const double2 l23 = __ldg(reinterpret_cast<const double2*>(P.lam + gcol + 2));
+              tq.x = rbe * x.x + rom * (float)l01.x * wv.x;
+              tq.y = rbe * x.y + rom * (float)l01.y * wv.y;
+              tq.z = rbe * x.z + rom * (float)l23.x * wv.z;
+              tq.w = rbe * x.w + rom * (float)l23.y * wv.w;
             }
-            tv[4 * q] = tq.x;
-            tv[4 * q + 1] = tq.y;
-            tv[4 * q + 2] = tq.z;
-            tv[4 * q + 3] = tq.w;
+            tv[4 * u] = tq.x;
+            tv[4 * u + 1] = tq.y;
+            tv[4 * u + 2] = tq.z;
+            tv[4 * u + 3] = tq.w;
           }
-          tc::tmem_st16(taddr + c * 32, tv);
-          tc::tmem_st16(taddr + c * 32 + 16, tv + 16);
+          tc::tmem_st16(taddr + c16 * 16, tv);
         }
         tc::tmem_wait_st();
-        // once every converter has read its row of the stage (a bounded wait on a barrier that
+        // once every converter has read its part of the stage (a bounded wait on a barrier that
         // completes one phase per tile), rewrite the stage as the K-major operand
         tc::mbar_arrive(&cvt_read);
         ok = tc::mbar_wait(&cvt_read, (uint32_t)(j & 1));
@@ -367,16 +370,13 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
           break;
         }
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int col = c * 32 + 4 * q;
-            const float4 x = v[c * 8 + q];
-            *reinterpret_cast<float*>(slot + img_off(col, k, BN)) = tf32_rna(x.x);
-            *reinterpret_cast<float*>(slot + img_off(col + 1, k, BN)) = tf32_rna(x.y);
-            *reinterpret_cast<float*>(slot + img_off(col + 2, k, BN)) = tf32_rna(x.z);
-            *reinterpret_cast<float*>(slot + img_off(col + 3, k, BN)) = tf32_rna(x.w);
-          }
+        for (int u = 0; u < HB / 4; ++u) {
+          const int col = h * HB + 4 * u;
+          const float4 x = v[u];
+          *reinterpret_cast<float*>(slot + img_off(col, k, BN)) = tf32_rna(x.x);
+          *reinterpret_cast<float*>(slot + img_off(col + 1, k, BN)) = tf32_rna(x.y);
+          *reinterpret_cast<float*>(slot + img_off(col + 2, k, BN)) = tf32_rna(x.z);
+          *reinterpret_cast<float*>(slot + img_off(col + 3, k, BN)) = tf32_rna(x.w);
         }
         fence_proxy_async();  // the generic-proxy writes, before the MMA reads them
         tc::tc_fence_before();
