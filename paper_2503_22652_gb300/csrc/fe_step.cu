@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)p.nA * kABytes;
+  float* sL = reinterpret_cast<float*>(sB + (size_t)p.nslots * kSlotBytes);  // Lambda of each stage's columns
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       tc::mbar_init(&accempty[i], 128);
     }
     for (int i = 0; i < 4; ++i) {
-      tc::mbar_init(&bfull[i], 1);
+      tc::mbar_init(&bfull[i], 2);  // the copies' expect_tx arrival and the Lambda stores
       tc::mbar_init(&bempty[i], 1);
       tc::mbar_init(&ifull[i], 256);
     }
@@ -242,6 +243,14 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
           gather4(dst + c * kChunkBytes, &P.vmap, t * BN + 32 * c, r[0], r[1], r[2], r[3], &bfull[s]);
           if (wl) gather4(dst + kHalf + c * kChunkBytes, &P.wmap, t * BN + 32 * c, w[0], w[1], w[2], w[3], &bfull[s]);
         }
+        // the tile's Lambda values (FP32) for the converters' owner terms
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int col = t * BN + 32 * c + lane;
+          sL[s * BN + 32 * c + lane] = col < P.n ? (float)__ldg(P.lam + col) : 0.f;
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bfull[s]);
       }
     }
     if (*vabort && lane == 0) {
@@ -345,12 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
             const int gcol = t * BN + col;
             if (o >= 0 && gcol < P.n) {
               const float4 wv = *reinterpret_cast<const float4*>(wrow + c * kChunkBytes + ((qd ^ (o & 7)) << 4));
-              const double2 l01 = __ldg(reinterpret_cast<const double2*>(P.lam + gcol));
-              const double2 l23 = __ldg(reinterpret_cast<const double2*>(P.lam + gcol + 2));
-              tq.x = rbe * x.x + rom * (float)l01.x * wv.x;
-              tq.y = rbe * x.y + rom * (float)l01.y * wv.y;
-              tq.z = rbe * x.z + rom * (float)l23.x * wv.z;
-              tq.w = rbe * x.w + rom * (float)l23.y * wv.w;
+              const float4 lv = *reinterpret_cast<const float4*>(sL + s * BN + col);
+              tq.x = rbe * x.x + rom * lv.x * wv.x;
+              tq.y = rbe * x.y + rom * lv.y * wv.y;
+              tq.z = rbe * x.z + rom * lv.z * wv.z;
+              tq.w = rbe * x.w + rom * lv.w * wv.w;
             }
             tv[4 * u] = tq.x;
             tv[4 * u + 1] = tq.y;
@@ -442,7 +450,7 @@ Plan make_plan(int BN) {
   const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
   const int pref[][2] = {{2, 4}, {2, 3}, {1, 4}, {1, 3}, {2, 2}, {1, 2}};
   for (const auto& c : pref) {
-    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * slot;
+    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * (slot + (size_t)BN * 4);
     if (need <= cap) return Plan{c[0], c[1], need + 1024};
   }
   return Plan{0, 0, 0};
