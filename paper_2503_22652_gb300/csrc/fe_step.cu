@@ -17,15 +17,16 @@
 // 128, packed once per operator as a K-major 128-byte-swizzled TF32 image), V_c (128 x BN) the
 // cell's rows of S_{k-1}, and T the owner terms of the cell's owned rows divided by alpha, so that
 // alpha D is the whole contribution of the cell.  The rows of V_c and the owned rows of W are
-// gathered from the row-major blocks by TMA (tile::gather4: four rows of 32 columns per copy,
-// 128-byte swizzle) into a ring of stages.  Converter threads (one cell node each) read their
+// gathered from the row-major blocks with 16-byte cp.async copies (a warp instruction moves whole
+// 128-byte row segments; a TMA tile::gather4 of four 128-byte rows per copy measured an order of
+// magnitude slower per byte) into a ring of 128-byte-swizzled stages.  Converter threads (one cell node each) read their
 // rows, store T into the accumulator with tcgen05.st, and, after a barrier among themselves,
 // rewrite the stage in place as the K-major TF32 operand of the MMA (the swizzled reads and the
 // operand writes are both free of shared-memory bank conflicts).
 //
 // Warp roles (448 threads):
-//   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile, lane l
-//              gathers the cell's nodes 4l..4l+3 of V and owned rows 4l..4l+3 of W;
+//   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile the
+//              cp.async copies of the V and W rows and the tile's Lambda values;
 //   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), accumulating
 //              onto the owner terms in one of two TMEM accumulators of BN columns;
 //   warps 2-9  converters (warp w: nodes 32 (w % 4).., the TMEM lanes it may access, and half of
@@ -34,8 +35,6 @@
 //              red.global.add.v4.f32 into the output rows.
 // Every mbarrier wait is bounded; on a timeout the kernel raises the error flag, waits (bounded)
 // for its copies and MMAs in flight, releases TMEM and returns.
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -83,8 +82,6 @@ __global__ void pack_scaled_kernel(int64_t n_cells, int nc, const double* __rest
 }
 
 struct StepPartDev {
-  CUtensorMap vmap;       // rows of V: 2D {n, rows}, box {32, 1}, 128-byte swizzle, zero fill
-  CUtensorMap wmap;       // rows of W, same form
   const int* dofs;
   const int* own_rows;    // per cell 128 entries: the dofs the cell owns, in node order, padded by
                           // repeating the last one (null: no owner terms in this part)
@@ -122,14 +119,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-// Four rows (r0..r3) of 32 columns starting at column x, into 512 consecutive bytes of shared memory.
-__device__ __forceinline__ void gather4(void* dst, const CUtensorMap* map, int x, int r0, int r1, int r2, int r3,
-                                        uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-      "%4, %5, %6}], [%7];" ::"r"(tc::smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(tc::smem_u32(bar))
-      : "memory");
+// 16-byte asynchronous copy global -> shared (L2 only); `in` = false writes 16 zero bytes instead.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool in) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(in ? 16 : 0)
+               : "memory");
+}
+
+// Arrive on `bar` once every cp.async this thread issued before has completed (the barrier's count
+// includes this arrival).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       cvt_read, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ int srow[kNCP], swrow[kNCP];  // the loader's current cell: dof rows, owned W rows
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       tc::mbar_init(&accempty[i], 128);
     }
     for (int i = 0; i < 4; ++i) {
-      tc::mbar_init(&bfull[i], 2);  // the copies' expect_tx arrival and the Lambda stores
+      tc::mbar_init(&bfull[i], 33);  // the 32 loader lanes' copies and the Lambda stores
       tc::mbar_init(&bempty[i], 1);
       tc::mbar_init(&ifull[i], 256);
     }
@@ -198,20 +199,24 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   const int nA = p.nA, nS = p.nslots;
 
   if (warp == 0) {
-    // ---------------- loader: cell images (bulk copies), gathered rows of V and owned rows of W
+    // ---------------- loader: per cell one bulk copy of the cell image; per tile the cell's rows of
+    // V and its owned rows of W as 16-byte cp.async copies (each warp instruction moves whole
+    // 128-byte row segments) into the 128-byte-swizzled staging layout, and the tile's Lambda values
+    constexpr int CPR = BN / 4;  // 16-byte chunks per row of a tile
     int64_t j = 0, cl = 0;
     bool stop = false;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
       const StepPartDev& P = p.part[part_of(p, g)];
       const int64_t cell = g - P.cell_off;
-      int r[4], w[4];
+      __syncwarp();
 #pragma unroll
-      for (int u = 0; u < 4; ++u) r[u] = __ldg(P.dofs + cell * P.nc + min(4 * lane + u, P.nc - 1));
+      for (int u = 0; u < 4; ++u) {
+        const int k = lane + 32 * u;  // padding nodes repeat the last real node's row
+        srow[k] = __ldg(P.dofs + cell * P.nc + min(k, P.nc - 1));
+        swrow[k] = P.own_rows ? __ldg(P.own_rows + cell * kNCP + k) : 0;
+      }
       const int cnt = P.own_rows ? __ldg(P.own_cnt + cell) : 0;
-      const bool wl = 4 * lane < cnt;  // this lane gathers owned rows 4l..4l+3 of W
-#pragma unroll
-      for (int u = 0; u < 4; ++u) w[u] = wl ? __ldg(P.own_rows + cell * kNCP + 4 * lane + u) : 0;
-      const uint32_t tile_bytes = kHalf + (uint32_t)((cnt + 3) / 4) * NCH * 512u;
+      __syncwarp();
       const int ab = (int)(cl % nA);
       int ok = 1;
       if (lane == 0) {
@@ -228,25 +233,31 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       }
       for (int t = 0; t < P.ntiles; ++t, ++j) {
         const int s = (int)(j % nS);
-        if (lane == 0) {
-          ok = !*vabort && tc::mbar_wait(&bempty[s], (uint32_t)((j / nS) & 1) ^ 1u);
-          if (ok) tc::mbar_arrive_expect_tx(&bfull[s], tile_bytes);
-        }
+        if (lane == 0) ok = !*vabort && tc::mbar_wait(&bempty[s], (uint32_t)((j / nS) & 1) ^ 1u);
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
           if (lane == 0) fail();
           stop = true;
           break;
         }
-        uint8_t* dst = sB + (size_t)s * kSlotBytes + lane * 512;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          gather4(dst + c * kChunkBytes, &P.vmap, t * BN + 32 * c, r[0], r[1], r[2], r[3], &bfull[s]);
-          if (wl) gather4(dst + kHalf + c * kChunkBytes, &P.wmap, t * BN + 32 * c, w[0], w[1], w[2], w[3], &bfull[s]);
+        uint8_t* slot = sB + (size_t)s * kSlotBytes;
+        const int c0 = t * BN;
+        // row k, chunk ch -> 32-column block ch / 8, 16-byte chunk (ch % 8) ^ (k % 8) of row k
+        for (int e = lane; e < kNCP * CPR; e += 32) {
+          const int k = e / CPR, ch = e % CPR, col = c0 + 4 * ch;
+          const bool in = col < P.n;
+          const float* src = P.V + (int64_t)srow[k] * P.n + (in ? col : 0);
+          cp_async16(slot + (ch >> 3) * kChunkBytes + k * 128 + (((ch & 7) ^ (k & 7)) << 4), src, in);
         }
-        // the tile's Lambda values (FP32) for the converters' owner terms
+        for (int e = lane; e < cnt * CPR; e += 32) {
+          const int o = e / CPR, ch = e % CPR, col = c0 + 4 * ch;
+          const bool in = col < P.n;
+          const float* src = P.W + (int64_t)swrow[o] * P.n + (in ? col : 0);
+          cp_async16(slot + kHalf + (ch >> 3) * kChunkBytes + o * 128 + (((ch & 7) ^ (o & 7)) << 4), src, in);
+        }
+        cp_async_arrive_noinc(&bfull[s]);  // arrives when this lane's copies have landed
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
-          const int col = t * BN + 32 * c + lane;
+          const int col = c0 + 32 * c + lane;
           sL[s * BN + 32 * c + lane] = col < P.n ? (float)__ldg(P.lam + col) : 0.f;
         }
         __syncwarp();
@@ -447,29 +458,13 @@ struct Plan {
 
 Plan make_plan(int BN) {
   const size_t slot = 2 * (size_t)(BN / 32) * kChunkBytes;
-  const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
+  const size_t cap = kSmemMax - 1024 - 1280;  // alignment slack and the kernel's static shared memory (1216 B)
   const int pref[][2] = {{2, 4}, {2, 3}, {1, 4}, {1, 3}, {2, 2}, {1, 2}};
   for (const auto& c : pref) {
     const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * (slot + (size_t)BN * 4);
     if (need <= cap) return Plan{c[0], c[1], need + 1024};
   }
   return Plan{0, 0, 0};
-}
-
-CUtensorMap row_map(const float* base, int64_t rows, int n) {
-  CUtensorMap m;
-  RC_CHECK(((uintptr_t)base & 15) == 0 && n % 4 == 0, RCHFSI_ERR_INVALID_ARG,
-           "fused FE step: block rows must start on 16-byte boundaries");
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)n * 4};
-  cuuint32_t box[2] = {32, 1};
-  cuuint32_t estr[2] = {1, 1};
-  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
-  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  RC_CHECK(r == CUDA_SUCCESS, RCHFSI_ERR_CUDA, "cuTensorMapEncodeTiled (gather map) failed (" + std::to_string((int)r) + ")");
-  return m;
 }
 
 const uint8_t* scaled_images(cudaStream_t s, FeOp& op, const double* dinv) {
@@ -485,7 +480,7 @@ const uint8_t* scaled_images(cudaStream_t s, FeOp& op, const double* dinv) {
 
 template <int BN>
 void launch(cudaStream_t s, const StepBatch& b, const Plan& pl, unsigned grid) {
-  set_smem_limit(reinterpret_cast<const void*>(fe_step_kernel<BN>), kSmemMax - 512);
+  set_smem_limit(reinterpret_cast<const void*>(fe_step_kernel<BN>), kSmemMax - 1280);
   fe_step_kernel<BN><<<grid, kThreads, pl.smem, s>>>(b);
   RC_LAUNCH();
 }
@@ -539,8 +534,8 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
     RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own_rows.p, RCHFSI_ERR_INVALID_ARG,
              "fused FE step: n_c <= 128, n a multiple of 4 and owner lists required");
     StepPartDev& P = b.part[q];
-    P.vmap = row_map(t.V, t.rows, t.n);
-    P.wmap = row_map(t.W, t.rows, t.n);
+    RC_CHECK(((uintptr_t)t.V & 15) == 0 && ((uintptr_t)t.W & 15) == 0 && ((uintptr_t)t.U & 15) == 0,
+             RCHFSI_ERR_INVALID_ARG, "fused FE step: blocks must start on 16-byte boundaries");
     P.dofs = op.dofs.p;
     P.own_rows = t.owner ? op.own_rows.p : nullptr;
     P.own_pos = op.own_pos.p;
