@@ -17,20 +17,21 @@
 // 128, packed once per operator as a K-major 128-byte-swizzled TF32 image), V_c (128 x BN) the
 // cell's rows of S_{k-1}, and T the owner terms of the cell's owned rows divided by alpha, so that
 // alpha D is the whole contribution of the cell.  The rows of V_c and the owned rows of W are
-// gathered from the row-major blocks with 16-byte cp.async copies (a warp instruction moves whole
-// 128-byte row segments; a TMA tile::gather4 of four 128-byte rows per copy measured an order of
-// magnitude slower per byte) into a ring of 128-byte-swizzled stages.  Converter threads (one cell node each) read their
-// rows, store T into the accumulator with tcgen05.st, and, after a barrier among themselves,
-// rewrite the stage in place as the K-major TF32 operand of the MMA (the swizzled reads and the
-// operand writes are both free of shared-memory bank conflicts).
+// gathered from the row-major blocks with 16-byte cp.async copies by 256 threads (a warp
+// instruction copies whole 256-byte row segments) into a ring of 128-byte-swizzled stages, up to
+// two tiles ahead of the tile being converted.  (A single loader warp issuing the copies, or TMA
+// tile::gather4 copies of four 128-byte rows, moved only ~6 bytes per clock per SM.)  The same
+// threads then convert: each (one cell node, half of the columns) reads its row, stores T into the
+// accumulator with tcgen05.st and, after a barrier among the converters, rewrites the stage in
+// place as the K-major TF32 operand of the MMA (the swizzled reads and the operand writes are both
+// free of shared-memory bank conflicts).
 //
 // Warp roles (448 threads):
-//   warp 0     loader: per cell one bulk copy of the cell image (nA buffers); per tile the
-//              cp.async copies of the V and W rows and the tile's Lambda values;
+//   warp 0     cell images: one bulk copy per cell (nA buffers);
 //   warp 1     MMA issuer (the whole warp walks the loop, one elected lane issues), accumulating
 //              onto the owner terms in one of two TMEM accumulators of BN columns;
-//   warps 2-9  converters (warp w: nodes 32 (w % 4).., the TMEM lanes it may access, and half of
-//              the tile's columns);
+//   warps 2-9  gather + convert (warp w: nodes 32 (w % 4).., the TMEM lanes it may access, and
+//              half of the tile's columns);
 //   warps 10-13 epilogue: TMEM lanes 32 (w % 4).. (one cell node per thread); alpha scaling and
 //              red.global.add.v4.f32 into the output rows.
 // Every mbarrier wait is bounded; on a timeout the kernel raises the error flag, waits (bounded)
@@ -83,10 +84,7 @@ __global__ void pack_scaled_kernel(int64_t n_cells, int nc, const double* __rest
 
 struct StepPartDev {
   const int* dofs;
-  const int* own_rows;    // per cell 128 entries: the dofs the cell owns, in node order, padded by
-                          // repeating the last one (null: no owner terms in this part)
-  const int8_t* own_pos;  // per cell 128 entries: position of node k in own_rows, -1 if not owned
-  const int* own_cnt;     // per cell: number of owned nodes
+  const int8_t* own_pos;  // per cell 128 entries: >= 0 when the cell owns its node k
   const uint8_t* img;
   const float* V;
   const float* W;
@@ -95,7 +93,7 @@ struct StepPartDev {
   const double* coef;
   int64_t n_cells, cell_off;
   float alpha, beta, omega, sign;
-  int nc, n, ntiles;
+  int nc, n, ntiles, owner;  // owner = 0: no owner terms in this part
 };
 
 struct StepBatch {
@@ -150,6 +148,8 @@ __device__ __forceinline__ uint32_t img_off(int r, int k, int rows) {
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_constant__ StepBatch p) {
   constexpr int NCH = BN / 32;
+  constexpr int CPR = BN / 4;                     // 16-byte chunks per row of a tile
+  constexpr int HB = BN / 2;                      // columns of one converter thread per tile
   constexpr uint32_t kHalf = NCH * kChunkBytes;   // 128 rows of BN FP32 values
   constexpr uint32_t kSlotBytes = 2 * kHalf;      // V rows (then the operand), owned W rows
   extern __shared__ uint8_t smem_raw[];
@@ -157,13 +157,12 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       cvt_read, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  __shared__ int srow[kNCP], swrow[kNCP];  // the loader's current cell: dof rows, owned W rows
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)p.nA * kABytes;
-  float* sL = reinterpret_cast<float*>(sB + (size_t)p.nslots * kSlotBytes);  // Lambda of each stage's columns
+  double* sL = reinterpret_cast<double*>(sB + (size_t)p.nslots * kSlotBytes);  // Lambda of each stage's columns
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -173,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       tc::mbar_init(&accempty[i], 128);
     }
     for (int i = 0; i < 4; ++i) {
-      tc::mbar_init(&bfull[i], 33);  // the 32 loader lanes' copies and the Lambda stores
+      tc::mbar_init(&bfull[i], 256);  // every gathering thread, once its copies have landed
       tc::mbar_init(&bempty[i], 1);
       tc::mbar_init(&ifull[i], 256);
     }
@@ -199,75 +198,21 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   const int nA = p.nA, nS = p.nslots;
 
   if (warp == 0) {
-    // ---------------- loader: per cell one bulk copy of the cell image; per tile the cell's rows of
-    // V and its owned rows of W as 16-byte cp.async copies (each warp instruction moves whole
-    // 128-byte row segments) into the 128-byte-swizzled staging layout, and the tile's Lambda values
-    constexpr int CPR = BN / 4;  // 16-byte chunks per row of a tile
-    int64_t j = 0, cl = 0;
-    bool stop = false;
-    for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G, ++cl) {
-      const StepPartDev& P = p.part[part_of(p, g)];
-      const int64_t cell = g - P.cell_off;
-      __syncwarp();
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int k = lane + 32 * u;  // padding nodes repeat the last real node's row
-        srow[k] = __ldg(P.dofs + cell * P.nc + min(k, P.nc - 1));
-        swrow[k] = P.own_rows ? __ldg(P.own_rows + cell * kNCP + k) : 0;
-      }
-      const int cnt = P.own_rows ? __ldg(P.own_cnt + cell) : 0;
-      __syncwarp();
-      const int ab = (int)(cl % nA);
-      int ok = 1;
-      if (lane == 0) {
-        ok = !*vabort && tc::mbar_wait(&aempty[ab], (uint32_t)((cl / nA) & 1) ^ 1u);
-        if (ok) {
-          tc::mbar_arrive_expect_tx(&afull[ab], kABytes);
-          bulk_g2s(sA + (size_t)ab * kABytes, P.img + cell * (int64_t)kABytes, kABytes, &afull[ab]);
-        }
-      }
-      if (!__shfl_sync(0xffffffffu, ok, 0)) {
-        if (lane == 0) fail();
-        stop = true;
-        break;
-      }
-      for (int t = 0; t < P.ntiles; ++t, ++j) {
-        const int s = (int)(j % nS);
-        if (lane == 0) ok = !*vabort && tc::mbar_wait(&bempty[s], (uint32_t)((j / nS) & 1) ^ 1u);
-        if (!__shfl_sync(0xffffffffu, ok, 0)) {
-          if (lane == 0) fail();
-          stop = true;
+    // ---------------- cell images: one bulk copy per cell into nA buffers
+    if (lane == 0) {
+      int64_t cl = 0;
+      for (int64_t g = blockIdx.x; g < p.total_cells; g += G, ++cl) {
+        const int ab = (int)(cl % nA);
+        if (*vabort || !tc::mbar_wait(&aempty[ab], (uint32_t)((cl / nA) & 1) ^ 1u)) {
+          fail();
           break;
         }
-        uint8_t* slot = sB + (size_t)s * kSlotBytes;
-        const int c0 = t * BN;
-        // row k, chunk ch -> 32-column block ch / 8, 16-byte chunk (ch % 8) ^ (k % 8) of row k
-        for (int e = lane; e < kNCP * CPR; e += 32) {
-          const int k = e / CPR, ch = e % CPR, col = c0 + 4 * ch;
-          const bool in = col < P.n;
-          const float* src = P.V + (int64_t)srow[k] * P.n + (in ? col : 0);
-          cp_async16(slot + (ch >> 3) * kChunkBytes + k * 128 + (((ch & 7) ^ (k & 7)) << 4), src, in);
-        }
-        for (int e = lane; e < cnt * CPR; e += 32) {
-          const int o = e / CPR, ch = e % CPR, col = c0 + 4 * ch;
-          const bool in = col < P.n;
-          const float* src = P.W + (int64_t)swrow[o] * P.n + (in ? col : 0);
-          cp_async16(slot + kHalf + (ch >> 3) * kChunkBytes + o * 128 + (((ch & 7) ^ (o & 7)) << 4), src, in);
-        }
-        cp_async_arrive_noinc(&bfull[s]);  // arrives when this lane's copies have landed
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          const int col = c0 + 32 * c + lane;
-          sL[s * BN + 32 * c + lane] = col < P.n ? (float)__ldg(P.lam + col) : 0.f;
-        }
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&bfull[s]);
+        const StepPartDev& P = p.part[part_of(p, g)];
+        tc::mbar_arrive_expect_tx(&afull[ab], kABytes);
+        bulk_g2s(sA + (size_t)ab * kABytes, P.img + (g - P.cell_off) * (int64_t)kABytes, kABytes, &afull[ab]);
       }
-    }
-    if (*vabort && lane == 0) {
-      // let the copies already issued land before the CTA's shared memory is released (bounded)
-      for (int64_t c2 = (cl > nA ? cl - nA : 0); c2 < cl; ++c2) tc::mbar_wait(&afull[c2 % nA], (uint32_t)((c2 / nA) & 1));
-      for (int64_t j2 = (j > nS ? j - nS : 0); j2 < j; ++j2) tc::mbar_wait(&bfull[j2 % nS], (uint32_t)((j2 / nS) & 1));
+      if (*vabort)  // let the copies already issued land before the shared memory is released (bounded)
+        for (int64_t c2 = (cl > nA ? cl - nA : 0); c2 < cl; ++c2) tc::mbar_wait(&afull[c2 % nA], (uint32_t)((c2 / nA) & 1));
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer: accumulates onto the owner terms the converters stored
@@ -315,18 +260,66 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     }
     __syncwarp();
   } else if (warp < 10) {
-    // ---------------- converters: thread (k, h) owns cell node k (and TMEM lane k) and half h of
-    // the tile's columns
-    constexpr int HB = BN / 2;
+    // ---------------- gather + convert (256 threads)
+    // Gather (all 256 threads, coalesced: a warp instruction copies whole 256-byte row segments):
+    // the tile's rows of V and owned rows of W as 16-byte cp.async copies into the 128-byte-swizzled
+    // stage, and the tile's Lambda values; each thread arrives on the stage's barrier once its copies
+    // have landed.  Tiles are gathered `ahead` tiles ahead of the one being converted.
+    // Convert (thread (k, h): cell node k = TMEM lane k, half h of the columns): the owner terms
+    // into the accumulator (tcgen05.st), then, once all threads have read the stage, the stage
+    // rewritten in place as the K-major TF32 operand.
+    const int gt = threadIdx.x - 64;         // 0..255
     const int k = (warp & 3) * 32 + lane;
     const int h = (warp - 2) >> 2;
-    int64_t j = 0;
+    const int ahead = min(2, nS - 1);  // tiles gathered ahead: tile j + ahead reuses the stage of tile j - 1
+    // gather cursor (the tile kAhead ahead) and convert cursor
+    int64_t gg = blockIdx.x, jg = 0;
+    int tg = 0;
+    auto gather = [&]() -> bool {
+      if (gg >= p.total_cells) return true;
+      const StepPartDev& P = p.part[part_of(p, gg)];
+      const int s = (int)(jg % nS);
+      if (!tc::mbar_wait(&bempty[s], (uint32_t)((jg / nS) & 1) ^ 1u)) return false;
+      const int64_t cell = gg - P.cell_off;
+      const int c0 = tg * BN;
+      uint8_t* slot = sB + (size_t)s * kSlotBytes;
+#pragma unroll
+      for (int it = 0; it < kNCP * CPR / 256; ++it) {
+        const int e = it * 256 + gt;
+        const int kr = e / CPR, ch = e % CPR, col = c0 + 4 * ch;
+        const bool in = col < P.n;
+        const int kc = min(kr, P.nc - 1);  // padding nodes repeat the last real node's row
+        const int64_t row = (int64_t)__ldg(P.dofs + cell * P.nc + kc) * P.n;
+        const uint32_t off = (uint32_t)(ch >> 3) * kChunkBytes + (uint32_t)kr * 128 + (uint32_t)(((ch & 7) ^ (kr & 7)) << 4);
+        cp_async16(slot + off, P.V + row + (in ? col : 0), in);
+        if (P.owner && kr < P.nc && __ldg(P.own_pos + cell * kNCP + kr) >= 0)
+          cp_async16(slot + kHalf + off, P.W + row + (in ? col : 0), in);
+      }
+      for (int e = gt; e < BN / 2; e += 256) {
+        const int col = c0 + 2 * e;
+        const bool in = col < P.n;
+        cp_async16(sL + (size_t)s * BN + 2 * e, P.lam + (in ? col : 0), in);
+      }
+      cp_async_arrive_noinc(&bfull[s]);
+      ++jg;
+      if (++tg == P.ntiles) {
+        tg = 0;
+        gg += G;
+      }
+      return true;
+    }; 
     bool stop = false;
+    for (int a = 0; a < ahead && !stop; ++a)
+      if (!gather()) {
+        fail();
+        stop = true;
+      }
+    int64_t j = 0;
     for (int64_t g = blockIdx.x; g < p.total_cells && !stop; g += G) {
       const StepPartDev& P = p.part[part_of(p, g)];
       const int64_t cell = g - P.cell_off;
       const bool real = k < P.nc;
-      const int o = (real && P.own_rows) ? (int)__ldg(P.own_pos + cell * kNCP + k) : -1;
+      const bool own = real && P.owner && __ldg(P.own_pos + cell * kNCP + k) >= 0;
       float al = P.alpha, be = P.beta, om = P.omega;
       if (P.coef) {
         al = (float)__ldg(P.coef);
@@ -347,7 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         tc::tc_fence_after();
         uint8_t* slot = sB + (size_t)s * kSlotBytes;
         const uint8_t* vrow = slot + (size_t)k * 128;
-        const uint8_t* wrow = slot + kHalf + (size_t)(o < 0 ? 0 : o) * 128;
+        const uint8_t* wrow = slot + kHalf + (size_t)k * 128;
+        const double* lam = sL + (size_t)s * BN;
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(xb * BN + h * HB);
         float4 v[HB / 4];
 #pragma unroll
@@ -357,19 +351,20 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
           for (int u = 0; u < 4; ++u) {
             const int col = h * HB + c16 * 16 + 4 * u;      // column within the tile
             const int c = col >> 5, qd = (col & 31) >> 2;  // 32-column chunk, 16-byte chunk in the row
-            // 16-byte chunk qd of a staged row r sits at chunk qd ^ (r % 8) (the 128-byte swizzle)
-            float4 x = *reinterpret_cast<const float4*>(vrow + c * kChunkBytes + ((qd ^ (k & 7)) << 4));
+            // 16-byte chunk qd of staged row k sits at chunk qd ^ (k % 8) (the 128-byte swizzle)
+            const uint32_t off = (uint32_t)c * kChunkBytes + (uint32_t)((qd ^ (k & 7)) << 4);
+            float4 x = *reinterpret_cast<const float4*>(vrow + off);
             if (!real) x = make_float4(0.f, 0.f, 0.f, 0.f);
             v[c16 * 4 + u] = x;
             float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int gcol = t * BN + col;
-            if (o >= 0 && gcol < P.n) {
-              const float4 wv = *reinterpret_cast<const float4*>(wrow + c * kChunkBytes + ((qd ^ (o & 7)) << 4));
-              const float4 lv = *reinterpret_cast<const float4*>(sL + s * BN + col);
-              tq.x = rbe * x.x + rom * lv.x * wv.x;
-              tq.y = rbe * x.y + rom * lv.y * wv.y;
-              tq.z = rbe * x.z + rom * lv.z * wv.z;
-              tq.w = rbe * x.w + rom * lv.w * wv.w;
+            if (own) {
+              const float4 wv = *reinterpret_cast<const float4*>(wrow + off);
+              const double2 l01 = *reinterpret_cast<const double2*>(lam + col);
+              const double2 l23 = *reinterpret_cast<const double2*>(lam + col + 2);
+              tq.x = rbe * x.x + rom * (float)l01.x * wv.x;
+              tq.y = rbe * x.y + rom * (float)l01.y * wv.y;
+              tq.z = rbe * x.z + rom * (float)l23.x * wv.z;
+              tq.w = rbe * x.w + rom * (float)l23.y * wv.w;
             }
             tv[4 * u] = tq.x;
             tv[4 * u + 1] = tq.y;
@@ -400,8 +395,15 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         fence_proxy_async();  // the generic-proxy writes, before the MMA reads them
         tc::tc_fence_before();
         tc::mbar_arrive(&ifull[s]);
+        // the tile `ahead` further on, into the stage of tile j - 1 (free once its MMA is done)
+        if (!gather()) {
+          fail();
+          stop = true;
+        }
       }
     }
+    // copies still in flight land before the shared memory is released
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
     // ---------------- epilogue
     const int q = warp & 3;              // TMEM lane quarter this warp may access
@@ -458,10 +460,10 @@ struct Plan {
 
 Plan make_plan(int BN) {
   const size_t slot = 2 * (size_t)(BN / 32) * kChunkBytes;
-  const size_t cap = kSmemMax - 1024 - 1280;  // alignment slack and the kernel's static shared memory (1216 B)
+  const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
   const int pref[][2] = {{2, 4}, {2, 3}, {1, 4}, {1, 3}, {2, 2}, {1, 2}};
   for (const auto& c : pref) {
-    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * (slot + (size_t)BN * 4);
+    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * (slot + (size_t)BN * 8);
     if (need <= cap) return Plan{c[0], c[1], need + 1024};
   }
   return Plan{0, 0, 0};
@@ -480,7 +482,7 @@ const uint8_t* scaled_images(cudaStream_t s, FeOp& op, const double* dinv) {
 
 template <int BN>
 void launch(cudaStream_t s, const StepBatch& b, const Plan& pl, unsigned grid) {
-  set_smem_limit(reinterpret_cast<const void*>(fe_step_kernel<BN>), kSmemMax - 1280);
+  set_smem_limit(reinterpret_cast<const void*>(fe_step_kernel<BN>), kSmemMax - 512);
   fe_step_kernel<BN><<<grid, kThreads, pl.smem, s>>>(b);
   RC_LAUNCH();
 }
@@ -491,7 +493,7 @@ std::map<std::tuple<int, int64_t, int, int>, int> g_tune;
 }  // namespace
 
 bool fe_step_supported(const FeOp& op, int n, int precision) {
-  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own_rows.p != nullptr;
+  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own_pos.p != nullptr;
 }
 
 void fe_step_prepare(cudaStream_t s, FeOp& op) {
@@ -531,15 +533,14 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
   for (int q = 0; q < nparts; ++q) {
     const FeStepPart& t = parts[q];
     FeOp& op = *t.op;
-    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own_rows.p, RCHFSI_ERR_INVALID_ARG,
-             "fused FE step: n_c <= 128, n a multiple of 4 and owner lists required");
+    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own_pos.p, RCHFSI_ERR_INVALID_ARG,
+             "fused FE step: n_c <= 128, n a multiple of 4 and owner flags required");
     StepPartDev& P = b.part[q];
     RC_CHECK(((uintptr_t)t.V & 15) == 0 && ((uintptr_t)t.W & 15) == 0 && ((uintptr_t)t.U & 15) == 0,
              RCHFSI_ERR_INVALID_ARG, "fused FE step: blocks must start on 16-byte boundaries");
     P.dofs = op.dofs.p;
-    P.own_rows = t.owner ? op.own_rows.p : nullptr;
     P.own_pos = op.own_pos.p;
-    P.own_cnt = op.own_cnt.p;
+    P.owner = t.owner ? 1 : 0;
     // the scaled images use the D^-1 of the rows the part reads (both halves share it)
     P.img = scaled_images(s, op, op.Dinv.p);
     P.V = t.V;
