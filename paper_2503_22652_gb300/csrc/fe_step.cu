@@ -54,6 +54,7 @@ constexpr int kThreads = 448;                   // 14 warps
 constexpr uint32_t kABytes = kNCP * kNCP * 4;   // TF32 cell image
 constexpr uint32_t kChunkBytes = kNCP * 128;    // 32 columns of V_c: 128 rows of 128 bytes
 constexpr int kMaxParts = 64;
+constexpr int kMaxStages = 6;
 constexpr int kSmemMax = 232448;                // dynamic + static shared memory per CTA
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -153,8 +154,8 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   constexpr uint32_t kHalf = NCH * kChunkBytes;   // 128 rows of BN FP32 values
   constexpr uint32_t kSlotBytes = 2 * kHalf;      // V rows (then the operand), owned W rows
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[4], bempty[4], ifull[4], accfull[2], accempty[2],
-      cvt_read, mma_done;
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[kMaxStages], bempty[kMaxStages], ifull[kMaxStages],
+      accfull[2], accempty[2], cvt_read, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       tc::mbar_init(&accfull[i], 1);
       tc::mbar_init(&accempty[i], 128);
     }
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kMaxStages; ++i) {
       tc::mbar_init(&bfull[i], 256);  // every gathering thread, once its copies have landed
       tc::mbar_init(&bempty[i], 1);
       tc::mbar_init(&ifull[i], 256);
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     const int gt = threadIdx.x - 64;         // 0..255
     const int k = (warp & 3) * 32 + lane;
     const int h = (warp - 2) >> 2;
-    const int ahead = min(2, nS - 1);  // tiles gathered ahead: tile j + ahead reuses the stage of tile j - 1
+    const int ahead = nS - 1;  // tiles gathered ahead: tile j + ahead reuses the stage of tile j - 1
     // gather cursor (the tile kAhead ahead) and convert cursor
     int64_t gg = blockIdx.x, jg = 0;
     int tg = 0;
@@ -459,12 +460,15 @@ struct Plan {
 };
 
 Plan make_plan(int BN) {
-  const size_t slot = 2 * (size_t)(BN / 32) * kChunkBytes;
+  // the deepest ring of stages that fits beside one cell image (the gathers run nslots - 1 tiles
+  // ahead); a second image buffer only when it leaves at least three stages
+  const size_t stage = 2 * (size_t)(BN / 32) * kChunkBytes + (size_t)BN * 8;
   const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
-  const int pref[][2] = {{2, 4}, {2, 3}, {1, 4}, {1, 3}, {2, 2}, {1, 2}};
-  for (const auto& c : pref) {
-    const size_t need = (size_t)c[0] * kABytes + (size_t)c[1] * (slot + (size_t)BN * 8);
-    if (need <= cap) return Plan{c[0], c[1], need + 1024};
+  for (int nA : {1, 2}) {
+    for (int ns = kMaxStages; ns >= (nA == 2 ? 3 : 2); --ns) {
+      const size_t need = (size_t)nA * kABytes + (size_t)ns * stage;
+      if (need <= cap) return Plan{nA, ns, need + 1024};
+    }
   }
   return Plan{0, 0, 0};
 }
