@@ -420,12 +420,14 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
     cast_f64_to_f32(c.s, blk, Wr, Wl, 1.0, 0);
     fill_zero(c.s, RX, blk * sizeof(float));       // S_0 = R_0 = 0
     if (!co.empty()) {
-      const int BN = fe_step_tune(c.s, c.num_sms, f, N, RY, Wl, lamtab + N);
+      float* lamf = c.w.lamtab_f.ensure((size_t)(p + 1) * N);  // the Lambda table in FP32 for the kernel
+      cast_f64_to_f32(c.s, (int64_t)(p + 1) * N, lamtab, lamf, 1.0, 0);
+      const int BN = fe_step_tune(c.s, c.num_sms, f, N, RY, Wl, lamf + N);
       for (int k = 2; k <= p; ++k) {
         double cf[3];
         fused_coefs(co, sc, k, cf);
         FeStepPart parts[4];
-        const int np = fe_step_parts(f, RY, Wl, RX, lamtab + (size_t)(k - 1) * N, N, (float)cf[0], (float)cf[1],
+        const int np = fe_step_parts(f, RY, Wl, RX, lamf + (size_t)(k - 1) * N, N, (float)cf[0], (float)cf[1],
                                      (float)cf[2], nullptr, parts);
         fe_step_batch(c.s, parts, np, BN, c.num_sms);
         std::swap(RX, RY);
@@ -618,8 +620,13 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     cast_f64_to_f32(s, blk, Wr, RY[q], s1 / e, 0);
     cast_f64_to_f32(s, blk, Wr, WL[q], 1.0, 0);
     fill_zero(s, RX[q], blk * sizeof(float));
-    if (fused) fe_step_prepare(s, *c.fe);
-    else fe_tc_parts_prepare(s, *c.fe, prec);
+    if (fused) {
+      fe_step_prepare(s, *c.fe);
+      float* lf = c.w.lamtab_f.ensure(tabs[q].size());  // the Lambda table in FP32 for the kernel
+      cast_f64_to_f32(s, (int64_t)tabs[q].size(), dtab[q], lf, 1.0, 0);
+    } else {
+      fe_tc_parts_prepare(s, *c.fe, prec);
+    }
   }
   // 2. column tiles (autotuned once per shape); the fused launch takes one tile for all problems,
   //    the one tuned for the problem with the most cells
@@ -627,7 +634,7 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
   int64_t most = -1;
   for (int q = 0; q < nj; ++q) {
     FeOp& op = *jobs[q].c->fe;
-    bn[q] = fused ? fe_step_tune(s, num_sms, op, nn[q], RY[q], WL[q], dtab[q] + nn[q])
+    bn[q] = fused ? fe_step_tune(s, num_sms, op, nn[q], RY[q], WL[q], jobs[q].c->w.lamtab_f.p + nn[q])
                   : tune_bn(s, num_sms, op, prec, nn[q], RY[q]);
     if (op.n_cells * (op.cplx ? 4 : 1) > most) {
       most = op.n_cells * (op.cplx ? 4 : 1);
@@ -640,7 +647,8 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
   std::vector<uintptr_t> key = {(uintptr_t)p, (uintptr_t)prec, (uintptr_t)fused};
   for (int q = 0; q < nj; ++q)
     for (uintptr_t v : {(uintptr_t)jobs[q].c, (uintptr_t)RX[q], (uintptr_t)RY[q], (uintptr_t)WL[q],
-                        (uintptr_t)dtab[q], (uintptr_t)dcoef[q], (uintptr_t)nn[q], (uintptr_t)bn[q]})
+                        (uintptr_t)dtab[q], (uintptr_t)dcoef[q], (uintptr_t)nn[q], (uintptr_t)bn[q],
+                        (uintptr_t)jobs[q].c->w.lamtab_f.p})
       key.push_back(v);
   if (!plan.exec || plan.key != key) {
     if (plan.exec) {
@@ -658,8 +666,8 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
         for (int q = 0; q < nj; ++q) {
           rchfsi_ctx& c = *jobs[q].c;
           FeStepPart pp[4];
-          const int np = fe_step_parts(*c.fe, ry[q], WL[q], rx[q], dtab[q] + (size_t)(k + 1) * nn[q], nn[q], 0.f,
-                                       0.f, 0.f, dcoef[q] + 3 * k, pp);
+          const int np = fe_step_parts(*c.fe, ry[q], WL[q], rx[q], c.w.lamtab_f.p + (size_t)(k + 1) * nn[q], nn[q],
+                                       0.f, 0.f, 0.f, dcoef[q] + 3 * k, pp);
           parts.insert(parts.end(), pp, pp + np);
         }
         for (size_t o = 0; o < parts.size(); o += 64) {

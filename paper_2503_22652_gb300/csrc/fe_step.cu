@@ -90,7 +90,7 @@ struct StepPartDev {
   const float* V;
   const float* W;
   float* U;
-  const double* lam;
+  const float* lam;
   const double* coef;
   int64_t n_cells, cell_off;
   float alpha, beta, omega, sign;
@@ -120,9 +120,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 // 16-byte asynchronous copy global -> shared (L2 only); `in` = false writes 16 zero bytes instead.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool in) {
+  // no memory clobber: the copy is ordered by the mbarrier that completes with it, and loads that
+  // feed later copies may be scheduled ahead of it
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)),
-               "l"(reinterpret_cast<uint64_t>(src)), "r"(in ? 16 : 0)
-               : "memory");
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(in ? 16 : 0));
 }
 
 // Arrive on `bar` once every cp.async this thread issued before has completed (the barrier's count
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + (size_t)p.nA * kABytes;
-  double* sL = reinterpret_cast<double*>(sB + (size_t)p.nslots * kSlotBytes);  // Lambda of each stage's columns
+  float* sL = reinterpret_cast<float*>(sB + (size_t)p.nslots * kSlotBytes);  // Lambda of each stage's columns
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -296,10 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         if (P.owner && kr < P.nc && __ldg(P.own_pos + cell * kNCP + kr) >= 0)
           cp_async16(slot + kHalf + off, P.W + row + (in ? col : 0), in);
       }
-      for (int e = gt; e < BN / 2; e += 256) {
-        const int col = c0 + 2 * e;
+      for (int e = gt; e < BN / 4; e += 256) {
+        const int col = c0 + 4 * e;
         const bool in = col < P.n;
-        cp_async16(sL + (size_t)s * BN + 2 * e, P.lam + (in ? col : 0), in);
+        cp_async16(sL + (size_t)s * BN + 4 * e, P.lam + (in ? col : 0), in);
       }
       cp_async_arrive_noinc(&bfull[s]);
       ++jg;
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         uint8_t* slot = sB + (size_t)s * kSlotBytes;
         const uint8_t* vrow = slot + (size_t)k * 128;
         const uint8_t* wrow = slot + kHalf + (size_t)k * 128;
-        const double* lam = sL + (size_t)s * BN;
+        const float* lam = sL + (size_t)s * BN;
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(xb * BN + h * HB);
         float4 v[HB / 4];
 #pragma unroll
@@ -359,13 +360,13 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
             v[c16 * 4 + u] = x;
             float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
             if (own) {
+              // (FP32 Lambda: a conversion from FP64 would hold the SM's FP64 pipe ~16 clocks per warp)
               const float4 wv = *reinterpret_cast<const float4*>(wrow + off);
-              const double2 l01 = *reinterpret_cast<const double2*>(lam + col);
-              const double2 l23 = *reinterpret_cast<const double2*>(lam + col + 2);
-              tq.x = rbe * x.x + rom * (float)l01.x * wv.x;
-              tq.y = rbe * x.y + rom * (float)l01.y * wv.y;
-              tq.z = rbe * x.z + rom * (float)l23.x * wv.z;
-              tq.w = rbe * x.w + rom * (float)l23.y * wv.w;
+              const float4 lv = *reinterpret_cast<const float4*>(lam + col);
+              tq.x = rbe * x.x + rom * lv.x * wv.x;
+              tq.y = rbe * x.y + rom * lv.y * wv.y;
+              tq.z = rbe * x.z + rom * lv.z * wv.z;
+              tq.w = rbe * x.w + rom * lv.w * wv.w;
             }
             tv[4 * u] = tq.x;
             tv[4 * u + 1] = tq.y;
@@ -462,7 +463,7 @@ struct Plan {
 Plan make_plan(int BN) {
   // the deepest ring of stages that fits beside one cell image (the gathers run nslots - 1 tiles
   // ahead); a second image buffer only when it leaves at least three stages
-  const size_t stage = 2 * (size_t)(BN / 32) * kChunkBytes + (size_t)BN * 8;
+  const size_t stage = 2 * (size_t)(BN / 32) * kChunkBytes + (size_t)BN * 4;
   const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
   for (int nA : {1, 2}) {
     for (int ns = kMaxStages; ns >= (nA == 2 ? 3 : 2); --ns) {
@@ -505,7 +506,7 @@ void fe_step_prepare(cudaStream_t s, FeOp& op) {
   if (op.cplx) scaled_images(s, *op.imag, op.Dinv.p);
 }
 
-int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const double* lam, int n, float alpha,
+int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const float* lam, int n, float alpha,
                   float beta, float omega, const double* coef, FeStepPart* out) {
   if (!op.cplx) {
     out[0] = FeStepPart{&op, V, W, U, lam, coef, op.m, n, alpha, beta, omega, 1.f, true};
@@ -582,7 +583,7 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
   }
 }
 
-int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, const float* W, const double* lam) {
+int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, const float* W, const float* lam) {
   const auto key = std::make_tuple(op.nc, (int64_t)op.n_cells, n, op.cplx ? 1 : 0);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -8,7 +8,7 @@ namespace rchfsi {
 // halves of the embedded block).  With S_j = s_j R_j the scaled iterates of Algorithm 3:
 //   U[dofs(c), :] += sign * alpha * (A_c D_c^-1) V[dofs(c), :]            for every cell c
 //   U[d, :]       += beta * V[d, :] + omega * W[d, :] diag(lam)          once per dof d (owner terms)
-// V, W, U: row-major FP32 blocks of `rows` rows and n columns; lam: n doubles.  When coef is set,
+// V, W, U: row-major FP32 blocks of `rows` rows and n columns; lam: n floats (Lambda_{k-1} in FP32).  When coef is set,
 // (alpha, beta, omega) = coef[0..2] are read on the device (a captured graph stays valid when the
 // coefficients change).  owner = false drops the owner terms (the cross parts of a complex operator).
 struct FeStepPart {
@@ -16,7 +16,7 @@ struct FeStepPart {
   const float* V;
   const float* W;
   float* U;
-  const double* lam;
+  const float* lam;
   const double* coef;
   int64_t rows;
   int n;
@@ -29,7 +29,7 @@ struct FeStepPart {
 bool fe_step_supported(const FeOp& op, int n, int precision);
 
 // The parts of one operator's step (1 real, 4 complex); returns the count.
-int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const double* lam, int n, float alpha,
+int fe_step_parts(FeOp& op, const float* V, const float* W, float* U, const float* lam, int n, float alpha,
                   float beta, float omega, const double* coef, FeStepPart* out);
 
 // Pack the operator's scaled cell images (A_c D_c^-1, TF32) and owner masks ahead of a capture.
@@ -40,6 +40,6 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
 
 // Column tile for this operator and width, chosen by timing the candidates once per shape on the
 // problem's own data (into a scratch output); cached.
-int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, const float* W, const double* lam);
+int fe_step_tune(cudaStream_t s, int num_sms, FeOp& op, int n, const float* V, const float* W, const float* lam);
 
 }  // namespace rchfsi

@@ -21,6 +21,7 @@ struct Work {
   DevBuf<double> GA, GB, Z, Zt, Lb, Li;        // N x N (Lb: Cholesky factor, Li: its inverse)
   DevBuf<double> eigws;                        // workspace of the projected eigensolver
   DevBuf<double> evals, nrm, rabs, xnrm, lamtab;
+  DevBuf<float> lamtab_f;                      // FP32 copy of lamtab for the fused FE step
   DevBuf<float> R32a, R32b, W32;               // low-precision filter buffers (col-major or row-major)
   DevBuf<__nv_bfloat16> R16a, R16b, W16;
   DevBuf<float> split;                         // split-K partial sums of the tensor-core product
