@@ -274,28 +274,39 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     const int k = (warp & 3) * 32 + lane;
     const int h = (warp - 2) >> 2;
     const int ahead = nS - 1;  // tiles gathered ahead: tile j + ahead reuses the stage of tile j - 1
-    // gather cursor (the tile kAhead ahead) and convert cursor
+    // gather cursor (the tile `ahead` tiles ahead of the one converted): this thread copies the rows
+    // kr = (it * 256 + gt) / CPR of every tile, the same for all tiles of a cell, so their offsets
+    // and owner flags are loaded once per cell
+    constexpr int kIt = kNCP * CPR / 256;
     int64_t gg = blockIdx.x, jg = 0;
     int tg = 0;
+    int64_t rowoff[kIt];
+    uint32_t ownbits = 0;
     auto gather = [&]() -> bool {
       if (gg >= p.total_cells) return true;
       const StepPartDev& P = p.part[part_of(p, gg)];
       const int s = (int)(jg % nS);
-      if (!tc::mbar_wait(&bempty[s], (uint32_t)((jg / nS) & 1) ^ 1u)) return false;
       const int64_t cell = gg - P.cell_off;
+      if (tg == 0) {
+        ownbits = 0;
+#pragma unroll
+        for (int it = 0; it < kIt; ++it) {
+          const int kr = (it * 256 + gt) / CPR;
+          rowoff[it] = (int64_t)__ldg(P.dofs + cell * P.nc + min(kr, P.nc - 1)) * P.n;  // padding rows repeat
+          if (P.owner && kr < P.nc && __ldg(P.own_pos + cell * kNCP + kr) >= 0) ownbits |= 1u << it;
+        }
+      }
+      if (!tc::mbar_wait(&bempty[s], (uint32_t)((jg / nS) & 1) ^ 1u)) return false;
       const int c0 = tg * BN;
       uint8_t* slot = sB + (size_t)s * kSlotBytes;
 #pragma unroll
-      for (int it = 0; it < kNCP * CPR / 256; ++it) {
+      for (int it = 0; it < kIt; ++it) {
         const int e = it * 256 + gt;
         const int kr = e / CPR, ch = e % CPR, col = c0 + 4 * ch;
         const bool in = col < P.n;
-        const int kc = min(kr, P.nc - 1);  // padding nodes repeat the last real node's row
-        const int64_t row = (int64_t)__ldg(P.dofs + cell * P.nc + kc) * P.n;
         const uint32_t off = (uint32_t)(ch >> 3) * kChunkBytes + (uint32_t)kr * 128 + (uint32_t)(((ch & 7) ^ (kr & 7)) << 4);
-        cp_async16(slot + off, P.V + row + (in ? col : 0), in);
-        if (P.owner && kr < P.nc && __ldg(P.own_pos + cell * kNCP + kr) >= 0)
-          cp_async16(slot + kHalf + off, P.W + row + (in ? col : 0), in);
+        cp_async16(slot + off, P.V + rowoff[it] + (in ? col : 0), in);
+        if (ownbits & (1u << it)) cp_async16(slot + kHalf + off, P.W + rowoff[it] + (in ? col : 0), in);
       }
       for (int e = gt; e < BN / 4; e += 256) {
         const int col = c0 + 4 * e;
@@ -309,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         gg += G;
       }
       return true;
-    }; 
+    };
     bool stop = false;
     for (int a = 0; a < ahead && !stop; ++a)
       if (!gather()) {
