@@ -372,30 +372,46 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
   RC_CUDA(cudaStreamSynchronize(c.s));
   for (size_t i = 0; i < nd; ++i)
     RC_CHECK(hd[i] >= 0 && hd[i] < mc, RCHFSI_ERR_INVALID_ARG, "cell_dofs entry out of [0, m)");
-  // owner of each dof: the first cell (in cell order) that contains it
+  // owner of each dof, balanced over the cells: dofs in increasing order, each to the cell that
+  // contains it and owns the fewest dofs so far (the lowest cell index among equals); own_pos[c][k]
+  // = position of node k among the dofs cell c owns (node order), -1 when not owned
   {
     const size_t C = (size_t)f.n_cells;
-    std::vector<int> rows(C * 128, 0), cnt(C, 0);
+    std::vector<int> start((size_t)mc + 1, 0), cells(C * f.nc);
+    for (size_t i = 0; i < C * f.nc; ++i) ++start[(size_t)hd[i] + 1];
+    for (size_t d = 0; d < (size_t)mc; ++d) start[d + 1] += start[d];
+    {
+      std::vector<int> fill(start.begin(), start.end() - 1);
+      for (size_t cl = 0; cl < C; ++cl)
+        for (int k = 0; k < f.nc; ++k) cells[(size_t)fill[hd[cl * f.nc + k]]++] = (int)cl;
+    }
+    std::vector<int> cnt(C, 0), owner((size_t)mc, -1);
+    for (size_t d = 0; d < (size_t)mc; ++d) {
+      int best = -1;
+      for (int e = start[d]; e < start[d + 1]; ++e) {
+        const int cl = cells[(size_t)e];
+        if (best < 0 || cnt[cl] < cnt[best] || (cnt[cl] == cnt[best] && cl < best)) best = cl;
+      }
+      if (best >= 0) {
+        owner[d] = best;
+        ++cnt[best];
+      }
+    }
     std::vector<int8_t> pos(C * 128, -1);
-    std::vector<uint8_t> seen((size_t)mc, 0);
+    int most = 0;
     for (size_t cl = 0; cl < C; ++cl) {
       int n = 0;
       for (int k = 0; k < f.nc; ++k) {
         const int d = hd[cl * f.nc + k];
-        if (!seen[d]) {
-          seen[d] = 1;
-          pos[cl * 128 + k] = (int8_t)n;
-          rows[cl * 128 + n++] = d;
+        if (owner[d] == (int)cl) {
+          owner[d] = -2;  // a dof listed twice in one cell is owned once
+          pos[cl * 128 + k] = (int8_t)n++;
         }
       }
-      cnt[cl] = n;
-      for (int k = n; k < 128; ++k) rows[cl * 128 + k] = n ? rows[cl * 128 + n - 1] : hd[cl * f.nc];
+      most = std::max(most, n);
     }
-    RC_CUDA(cudaMemcpyAsync(f.own_rows.ensure(rows.size()), rows.data(), rows.size() * sizeof(int),
-                            cudaMemcpyHostToDevice, c.s));
+    f.own_max = most;
     RC_CUDA(cudaMemcpyAsync(f.own_pos.ensure(pos.size()), pos.data(), pos.size(), cudaMemcpyHostToDevice, c.s));
-    RC_CUDA(cudaMemcpyAsync(f.own_cnt.ensure(cnt.size()), cnt.data(), cnt.size() * sizeof(int),
-                            cudaMemcpyHostToDevice, c.s));
     RC_CUDA(cudaStreamSynchronize(c.s));
   }
   const size_t nb = f.B_shared ? (size_t)f.nc * f.nc : na;
@@ -419,10 +435,8 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
     to_device(c, op->A_cells, tmp.ensure(2 * na), 2 * na);
     cplx_deinterleave(c.s, na, tmp.p, f.A64.ensure(na), g.A64.ensure(na));
     RC_CUDA(cudaMemcpyAsync(g.dofs.ensure(nd), dofs, nd * sizeof(int), cudaMemcpyDeviceToDevice, c.s));
-    RC_CUDA(cudaMemcpyAsync(g.own_rows.ensure(f.own_rows.n), f.own_rows.p, f.own_rows.bytes(), cudaMemcpyDeviceToDevice,
-                            c.s));
     RC_CUDA(cudaMemcpyAsync(g.own_pos.ensure(f.own_pos.n), f.own_pos.p, f.own_pos.bytes(), cudaMemcpyDeviceToDevice, c.s));
-    RC_CUDA(cudaMemcpyAsync(g.own_cnt.ensure(f.own_cnt.n), f.own_cnt.p, f.own_cnt.bytes(), cudaMemcpyDeviceToDevice, c.s));
+    g.own_max = f.own_max;
     // D^-1 of the embedding: [D^-1; D^-1]
     double* dv = f.Dinv.ensure(2 * mc);
     to_device(c, op->Dinv, dv, mc);

@@ -22,11 +22,11 @@ struct FeOp {
   DevBuf<float> Dinv32;
   DevBuf<uint8_t> imgtf, img16;  // cell matrices packed as swizzled tensor-core operand images
   DevBuf<uint8_t> imgADtf;       // A_c D_c^-1 (columns scaled by D^-1 at the cell's dofs), TF32 images
-  // Owner of each dof: the first cell (in cell order) that contains it.  Per cell, 128 entries each:
-  // own_rows = the dofs the cell owns in node order (padded by repeating the last one), own_pos =
-  // the position of node k in own_rows (-1 when not owned); own_cnt = owned nodes per cell.
-  DevBuf<int> own_rows, own_cnt;
+  // Owner of each dof (one of the cells that contain it, balanced over the cells): per cell 128
+  // entries, own_pos[k] = position of node k among the dofs the cell owns (node order), -1 when it
+  // does not own it; own_max = the most dofs one cell owns.
   DevBuf<int8_t> own_pos;
+  int own_max = 0;
   int* err = nullptr;            // device flag raised when a bounded wait in a kernel runs out
   // Complex Hermitian operator A = Ar + i Ai acting on the real embedding [x_r; x_i] of length 2 mc:
   // this object holds Ar (A64) and B, `imag` holds Ai; m = 2 mc, Dinv = [D^-1; D^-1].  Each

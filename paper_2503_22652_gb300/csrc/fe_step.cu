@@ -53,6 +53,8 @@ constexpr int kNCP = 128;                       // padded cell size (MMA M and K
 constexpr int kThreads = 448;                   // 14 warps
 constexpr uint32_t kABytes = kNCP * kNCP * 4;   // TF32 cell image
 constexpr uint32_t kChunkBytes = kNCP * 128;    // 32 columns of V_c: 128 rows of 128 bytes
+constexpr int kWRows = 80;                      // owned rows of W staged per cell (at most)
+constexpr uint32_t kWChunkBytes = kWRows * 128;
 constexpr int kMaxParts = 64;
 constexpr int kMaxStages = 6;
 constexpr int kSmemMax = 232448;                // dynamic + static shared memory per CTA
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
   constexpr int CPR = BN / 4;                     // 16-byte chunks per row of a tile
   constexpr int HB = BN / 2;                      // columns of one converter thread per tile
   constexpr uint32_t kHalf = NCH * kChunkBytes;   // 128 rows of BN FP32 values
-  constexpr uint32_t kSlotBytes = 2 * kHalf;      // V rows (then the operand), owned W rows
+  constexpr uint32_t kSlotBytes = kHalf + NCH * kWChunkBytes;  // V rows (then the operand), owned W rows
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[kMaxStages], bempty[kMaxStages], ifull[kMaxStages],
       accfull[2], accempty[2], cvt_read, mma_done;
@@ -281,19 +283,18 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     int64_t gg = blockIdx.x, jg = 0;
     int tg = 0;
     int64_t rowoff[kIt];
-    uint32_t ownbits = 0;
+    int ownpos[kIt];
     auto gather = [&]() -> bool {
       if (gg >= p.total_cells) return true;
       const StepPartDev& P = p.part[part_of(p, gg)];
       const int s = (int)(jg % nS);
       const int64_t cell = gg - P.cell_off;
       if (tg == 0) {
-        ownbits = 0;
 #pragma unroll
         for (int it = 0; it < kIt; ++it) {
           const int kr = (it * 256 + gt) / CPR;
           rowoff[it] = (int64_t)__ldg(P.dofs + cell * P.nc + min(kr, P.nc - 1)) * P.n;  // padding rows repeat
-          if (P.owner && kr < P.nc && __ldg(P.own_pos + cell * kNCP + kr) >= 0) ownbits |= 1u << it;
+          ownpos[it] = (P.owner && kr < P.nc) ? (int)__ldg(P.own_pos + cell * kNCP + kr) : -1;
         }
       }
       if (!tc::mbar_wait(&bempty[s], (uint32_t)((jg / nS) & 1) ^ 1u)) return false;
@@ -306,7 +307,11 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         const bool in = col < P.n;
         const uint32_t off = (uint32_t)(ch >> 3) * kChunkBytes + (uint32_t)kr * 128 + (uint32_t)(((ch & 7) ^ (kr & 7)) << 4);
         cp_async16(slot + off, P.V + rowoff[it] + (in ? col : 0), in);
-        if (ownbits & (1u << it)) cp_async16(slot + kHalf + off, P.W + rowoff[it] + (in ? col : 0), in);
+        if (ownpos[it] >= 0) {  // owned row: W row into position ownpos of the compact W area
+          const int o = ownpos[it];
+          const uint32_t woff = (uint32_t)(ch >> 3) * kWChunkBytes + (uint32_t)o * 128 + (uint32_t)(((ch & 7) ^ (o & 7)) << 4);
+          cp_async16(slot + kHalf + woff, P.W + rowoff[it] + (in ? col : 0), in);
+        }
       }
       for (int e = gt; e < BN / 4; e += 256) {
         const int col = c0 + 4 * e;
@@ -332,7 +337,8 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       const StepPartDev& P = p.part[part_of(p, g)];
       const int64_t cell = g - P.cell_off;
       const bool real = k < P.nc;
-      const bool own = real && P.owner && __ldg(P.own_pos + cell * kNCP + k) >= 0;
+      const int o = (real && P.owner) ? (int)__ldg(P.own_pos + cell * kNCP + k) : -1;  // compact W row
+      const bool own = o >= 0;
       float al = P.alpha, be = P.beta, om = P.omega;
       if (P.coef) {
         al = (float)__ldg(P.coef);
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         tc::tc_fence_after();
         uint8_t* slot = sB + (size_t)s * kSlotBytes;
         const uint8_t* vrow = slot + (size_t)k * 128;
-        const uint8_t* wrow = slot + kHalf + (size_t)k * 128;
+        const uint8_t* wrow = slot + kHalf + (size_t)(own ? o : 0) * 128;
         const float* lam = sL + (size_t)s * BN;
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(xb * BN + h * HB);
         float4 v[HB / 4];
@@ -367,12 +373,13 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
             // 16-byte chunk qd of staged row k sits at chunk qd ^ (k % 8) (the 128-byte swizzle)
             const uint32_t off = (uint32_t)c * kChunkBytes + (uint32_t)((qd ^ (k & 7)) << 4);
             float4 x = *reinterpret_cast<const float4*>(vrow + off);
+            const uint32_t woff = (uint32_t)c * kWChunkBytes + (uint32_t)((qd ^ (o & 7)) << 4);
             if (!real) x = make_float4(0.f, 0.f, 0.f, 0.f);
             v[c16 * 4 + u] = x;
             float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
             if (own) {
               // (FP32 Lambda: a conversion from FP64 would hold the SM's FP64 pipe ~16 clocks per warp)
-              const float4 wv = *reinterpret_cast<const float4*>(wrow + off);
+              const float4 wv = *reinterpret_cast<const float4*>(wrow + woff);
               const float4 lv = *reinterpret_cast<const float4*>(lam + col);
               tq.x = rbe * x.x + rom * lv.x * wv.x;
               tq.y = rbe * x.y + rom * lv.y * wv.y;
@@ -474,7 +481,7 @@ struct Plan {
 Plan make_plan(int BN) {
   // the deepest ring of stages that fits beside one cell image (the gathers run nslots - 1 tiles
   // ahead); a second image buffer only when it leaves at least three stages
-  const size_t stage = 2 * (size_t)(BN / 32) * kChunkBytes + (size_t)BN * 4;
+  const size_t stage = (size_t)(BN / 32) * (kChunkBytes + kWChunkBytes) + (size_t)BN * 4;
   const size_t cap = kSmemMax - 1024 - 512;  // alignment slack and the kernel's static shared memory
   for (int nA : {1, 2}) {
     for (int ns = kMaxStages; ns >= (nA == 2 ? 3 : 2); --ns) {
@@ -509,7 +516,8 @@ std::map<std::tuple<int, int64_t, int, int>, int> g_tune;
 }  // namespace
 
 bool fe_step_supported(const FeOp& op, int n, int precision) {
-  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own_pos.p != nullptr;
+  return precision == RCHFSI_TF32 && n % 4 == 0 && n >= 4 && op.nc <= kNCP && op.own_pos.p != nullptr &&
+         op.own_max <= kWRows;
 }
 
 void fe_step_prepare(cudaStream_t s, FeOp& op) {
@@ -549,8 +557,8 @@ void fe_step_batch(cudaStream_t s, const FeStepPart* parts, int nparts, int BN, 
   for (int q = 0; q < nparts; ++q) {
     const FeStepPart& t = parts[q];
     FeOp& op = *t.op;
-    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own_pos.p, RCHFSI_ERR_INVALID_ARG,
-             "fused FE step: n_c <= 128, n a multiple of 4 and owner flags required");
+    RC_CHECK(op.nc <= kNCP && t.n % 4 == 0 && op.own_pos.p && op.own_max <= kWRows, RCHFSI_ERR_INVALID_ARG,
+             "fused FE step: n_c <= 128, n a multiple of 4, owner positions and at most 80 owned dofs per cell");
     StepPartDev& P = b.part[q];
     RC_CHECK(((uintptr_t)t.V & 15) == 0 && ((uintptr_t)t.W & 15) == 0 && ((uintptr_t)t.U & 15) == 0,
              RCHFSI_ERR_INVALID_ARG, "fused FE step: blocks must start on 16-byte boundaries");
