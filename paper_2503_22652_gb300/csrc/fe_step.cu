@@ -32,9 +32,8 @@
 //              onto the owner terms in one of two TMEM accumulators of BN columns;
 //   warps 2-9  gather + convert (warp w: nodes 32 (w % 4).., the TMEM lanes it may access, and
 //              half of the tile's columns);
-//   warps 10-13 epilogue: TMEM lanes 32 (w % 4).. (one cell node per thread); alpha scaling, a
-//              transpose through the tile's stage, and red.global.add.f32 of 32 consecutive
-//              columns of one row per instruction into the output rows.
+//   warps 10-13 epilogue: TMEM lanes 32 (w % 4).. (one cell node per thread); alpha scaling and
+//              red.global.add.v4.f32 into the output rows.
 // Every mbarrier wait is bounded; on a timeout the kernel raises the error flag, waits (bounded)
 // for its copies and MMAs in flight, releases TMEM and returns.
 #include <algorithm>
@@ -139,10 +138,6 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void red_add_f32(float* p, float a) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
-}
-
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
@@ -182,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     }
     for (int i = 0; i < kMaxStages; ++i) {
       tc::mbar_init(&bfull[i], 256);  // every gathering thread, once its copies have landed
-      tc::mbar_init(&bempty[i], 128);  // the epilogue threads, once they are done with the stage
+      tc::mbar_init(&bempty[i], 1);
       tc::mbar_init(&ifull[i], 256);
     }
     tc::mbar_init(&cvt_read, 256);
@@ -255,6 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
         }
         __syncwarp();
         if (leader) {
+          tc::mma_commit(&bempty[s]);
           tc::mma_commit(&accfull[xb]);
           if (t == P.ntiles - 1) tc::mma_commit(&aempty[ab]);
         }
@@ -429,11 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
     // copies still in flight land before the shared memory is released
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
-    // ---------------- epilogue: warp q takes accumulator rows (cell nodes) 32 q .. 32 q + 31.  The
-    // rows go through the tile's stage (free once the MMA is done; the MMA's operand is no longer
-    // needed) so that each red.global.add covers 32 consecutive columns of one row (one 128-byte
-    // request instead of 32): TMEM -> registers -> stage (16-byte chunks XOR-swizzled by row, free
-    // of bank conflicts both ways) -> red.global.add.f32.  The stage is then released to the gather.
+    // ---------------- epilogue
     const int q = warp & 3;              // TMEM lane quarter this warp may access
     const int i = q * 32 + lane;         // cell-local node of this thread's accumulator row
     int64_t j = 0;
@@ -443,9 +435,9 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
       const int64_t cell = g - P.cell_off;
       float al = P.coef ? (float)__ldg(P.coef) : P.alpha;
       al *= P.sign;
-      const int64_t myrow = (i < P.nc) ? (int64_t)__ldg(P.dofs + cell * P.nc + i) * P.n : -1;
+      const int64_t row = (i < P.nc) ? (int64_t)__ldg(P.dofs + cell * P.nc + i) * P.n : -1;
       for (int t = 0; t < P.ntiles; ++t, ++j) {
-        const int xb = (int)(j & 1), s = (int)(j % nS);
+        const int xb = (int)(j & 1);
         const int c0 = t * BN;
         bool ok = !*vabort && tc::mbar_wait(&accfull[xb], (uint32_t)((j >> 1) & 1));
         if (!ok) fail();
@@ -454,37 +446,22 @@ __global__ void __launch_bounds__(kThreads, 1) fe_step_kernel(const __grid_const
           break;
         }
         tc::tc_fence_after();
-        uint8_t* tb = sB + (size_t)s * kSlotBytes;  // 128 rows of BN values, row r at r * BN * 4
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(xb * BN);
 #pragma unroll
         for (int cc = 0; cc < BN; cc += 16) {
           float v[16];
           tc::tmem_ld16(taddr + cc, v);
+          if (row >= 0) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int col = cc + 4 * u;
-            const int seg = col >> 5, qd = (col & 31) >> 2;
-            *reinterpret_cast<float4*>(tb + (size_t)i * BN * 4 + seg * 128 + ((qd ^ (i & 7)) << 4)) =
-                make_float4(al * v[4 * u], al * v[4 * u + 1], al * v[4 * u + 2], al * v[4 * u + 3]);
+            for (int u = 0; u < 4; ++u) {
+              const int col = c0 + cc + 4 * u;
+              if (col < P.n)
+                red_add_v4(P.U + row + col, al * v[4 * u], al * v[4 * u + 1], al * v[4 * u + 2], al * v[4 * u + 3]);
+            }
           }
         }
         tc::tc_fence_before();
-        tc::mbar_arrive(&accempty[xb]);  // the accumulator is read: the next tile may use it
-        __syncwarp();
-        for (int r = 0; r < 32; ++r) {
-          const int64_t row = __shfl_sync(0xffffffffu, myrow, r);
-          const int ir = q * 32 + r;
-          if (row < 0) continue;  // padding node (warp-uniform)
-#pragma unroll
-          for (int seg = 0; seg < BN / 32; ++seg) {
-            const int col = seg * 32 + lane;
-            const float val = *reinterpret_cast<const float*>(tb + (size_t)ir * BN * 4 + seg * 128 +
-                                                              ((((lane >> 2) ^ (ir & 7))) << 4) + (lane & 3) * 4);
-            if (c0 + col < P.n) red_add_f32(P.U + row + c0 + col, val);
-          }
-        }
-        __syncwarp();
-        tc::mbar_arrive(&bempty[s]);  // stage free for the gather
+        tc::mbar_arrive(&accempty[xb]);
       }
     }
   }
