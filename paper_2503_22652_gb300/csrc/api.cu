@@ -829,10 +829,11 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
       }
       if (Na != N) oz_slice(c.s, N, m, Y, m, 1, w.ozL);  // every column for the Gram matrices
       // G_A = Y^T A Y, G_B = Y^T B Y (complex: the left N x Na half; the rest follows from J)
+      // (real problems: both are symmetric, only the tiles reaching the upper triangle are formed)
       oz_slice(c.s, Na, m, AY, m, 1, w.ozR);
-      oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GA.p, N, w.ozws, eflag);
+      oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GA.p, N, w.ozws, eflag, Na == N);
       oz_slice(c.s, Na, m, BY, m, 1, w.ozR);
-      oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag);
+      oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag, Na == N);
     } else {
       apply_A_f64(c, Y, AY, Na);
       jcomplete(AY);

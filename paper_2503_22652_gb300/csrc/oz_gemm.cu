@@ -140,6 +140,7 @@ struct OzArgs {
   double* C;       // final output (nsplit == 1) or partials [split][N][M]
   int64_t ldc;
   int partial;
+  int upper;       // only tiles that reach the upper triangle (i <= j) are computed
   int* err;
 };
 
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, split = blockIdx.z;
+  if (p.upper && m0 >= n0 + BN) return;  // strictly below the diagonal: mirrored afterwards
   const int c_begin = split * p.chunks_per_split;
   const int nch = min(p.nchunks, c_begin + p.chunks_per_split) - c_begin;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -448,9 +450,27 @@ int choose_split(int tiles, int nchunks, int num_sms, double* eff_out) {
   return nsplit;
 }
 
+// C(i, j) = C(j, i) for i > j (column-major n x n)
+__global__ void mirror_upper_kernel(int n, double* C, int64_t ldc) {
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / n), i = (int)(t - (int64_t)j * n);
+    if (i > j) C[(int64_t)j * ldc + i] = C[(int64_t)i * ldc + j];
+  }
+}
+
+// Output tiles of a product that reach the upper triangle (all of them unless `upper`).
+int kept_tiles(int m_tiles, int n_tiles, int BN, bool upper) {
+  if (!upper) return m_tiles * n_tiles;
+  int t = 0;
+  for (int bm = 0; bm < m_tiles; ++bm)
+    for (int bn = 0; bn < n_tiles; ++bn) t += (bm * BM < bn * BN + BN) ? 1 : 0;
+  return t;
+}
+
 template <int BN>
 void oz_gemm_launch(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
-                    DevBuf<double>& ws, int* err, int nsplit_in) {
+                    DevBuf<double>& ws, int* err, int nsplit_in, bool upper) {
   const int64_t M = A.R, N = B.R;
   const int m_tiles = (int)((M + BM - 1) / BM), n_tiles = (int)((N + BN - 1) / BN);
   const int nchunks = (int)(A.Kp / KC);
@@ -461,11 +481,7 @@ void oz_gemm_launch(cudaStream_t s, int num_sms, const OzOperand& A, const OzOpe
   const CUtensorMap ma = slice_map(A, BM);
   const CUtensorMap mb = slice_map(B, BN);
   const size_t smem = (size_t)ASTAGES * kABytes + 2 * (size_t)OzTile<BN>::kBBytes + 1024;
-  static const bool attr = [&] {
-    RC_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return true;
-  }();
-  (void)attr;
+  set_smem_limit(reinterpret_cast<const void*>(oz_gemm_kernel<BN>), (int)smem);
   OzArgs p;
   p.M = (int)M;
   p.N = (int)N;
@@ -477,6 +493,7 @@ void oz_gemm_launch(cudaStream_t s, int num_sms, const OzOperand& A, const OzOpe
   p.eb = B.ex.p;
   p.err = err;
   p.partial = nsplit > 1;
+  p.upper = upper ? 1 : 0;
   if (nsplit > 1) {
     p.C = ws.ensure((size_t)nsplit * M * N);
     p.ldc = M;
@@ -487,7 +504,9 @@ void oz_gemm_launch(cudaStream_t s, int num_sms, const OzOperand& A, const OzOpe
   dim3 grid(n_tiles, m_tiles, nsplit);
   {
     // tensor-core flops of the 28 slice products; bytes: the slices once and the FP64 output
-    prof::Scope ps(s, RCHFSI_KERNEL_GEMM_F64_EMU, 2.0 * M * N * A.Kp * (S * (S + 1) / 2),
+    // (a symmetric product computes the kept tiles only: the flops of those tiles)
+    const double frac = (double)kept_tiles(m_tiles, n_tiles, BN, upper) / ((double)m_tiles * n_tiles);
+    prof::Scope ps(s, RCHFSI_KERNEL_GEMM_F64_EMU, 2.0 * M * N * A.Kp * (S * (S + 1) / 2) * frac,
                    2.0 * S * (double)(M + N) * A.Kp + 8.0 * M * N);
     oz_gemm_kernel<BN><<<grid, kThreads, smem, s>>>(ma, mb, p);
     RC_LAUNCH();
@@ -498,29 +517,36 @@ void oz_gemm_launch(cudaStream_t s, int num_sms, const OzOperand& A, const OzOpe
     oz_sum_kernel<<<blocks, 256, 0, s>>>(M, N, nsplit, p.C, C, ldc);
     RC_LAUNCH();
   }
+  if (upper) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((M * N + 255) / 256, (int64_t)num_sms * 4);
+    mirror_upper_kernel<<<blocks, 256, 0, s>>>((int)M, C, ldc);
+    RC_LAUNCH();
+  }
 }
 
 }  // namespace
 
 void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
-             DevBuf<double>& ws, int* err) {
+             DevBuf<double>& ws, int* err, bool symmetric) {
   RC_CHECK(A.K == B.K && A.Kp == B.Kp, RCHFSI_ERR_INVALID_ARG, "oz_gemm: K mismatch");
   const int64_t M = A.R, N = B.R;
+  RC_CHECK(!symmetric || M == N, RCHFSI_ERR_INVALID_ARG, "oz_gemm: a symmetric product is square");
   RC_CHECK(M < (1LL << 31) && N < (1LL << 31), RCHFSI_ERR_INVALID_ARG, "oz_gemm: too large");
   const int m_tiles = (int)((M + BM - 1) / BM);
   const int nchunks = (int)(A.Kp / KC);
   // tile width: 64 unless its padded columns or its worse wave fill cost more than the wider MMAs
   // save (a 128 x 64 x 16 MMA takes 48 clocks, a 128 x 32 x 16 one 40: 1.67x the columns per clock)
   double e32 = 0.0, e64 = 0.0;
-  const int t32 = m_tiles * (int)((N + 31) / 32), t64 = m_tiles * (int)((N + 63) / 64);
+  const int t32 = kept_tiles(m_tiles, (int)((N + 31) / 32), 32, symmetric);
+  const int t64 = kept_tiles(m_tiles, (int)((N + 63) / 64), 64, symmetric);
   const int s32 = choose_split(t32, nchunks, num_sms, &e32);
   const int s64 = choose_split(t64, nchunks, num_sms, &e64);
   const double c32 = (double)((N + 31) / 32 * 32) / 1.0 / std::max(e32, 1e-3);
   const double c64 = (double)((N + 63) / 64 * 64) / 1.67 / std::max(e64, 1e-3);
   if (c64 < c32)
-    oz_gemm_launch<64>(s, num_sms, A, B, C, ldc, ws, err, s64);
+    oz_gemm_launch<64>(s, num_sms, A, B, C, ldc, ws, err, s64, symmetric);
   else
-    oz_gemm_launch<32>(s, num_sms, A, B, C, ldc, ws, err, s32);
+    oz_gemm_launch<32>(s, num_sms, A, B, C, ldc, ws, err, s32, symmetric);
 }
 
 }  // namespace rchfsi

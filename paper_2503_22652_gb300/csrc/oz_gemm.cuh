@@ -35,7 +35,9 @@ void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs,
 
 // C(i, j) = sum_k A(i, k) B(j, k), i < A.R, j < B.R, stored column-major: C[j * ldc + i].
 // ws: split-K workspace (grown as needed); err: device flag raised by a bounded-wait timeout.
+// symmetric: the caller knows C is symmetric (a Gram matrix Y^T (A Y) with A symmetric, A.R == B.R):
+// only the output tiles that reach the upper triangle are computed and the rest is mirrored.
 void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
-             DevBuf<double>& ws, int* err);
+             DevBuf<double>& ws, int* err, bool symmetric = false);
 
 }  // namespace rchfsi
