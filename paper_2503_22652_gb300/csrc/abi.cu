@@ -385,6 +385,9 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
       for (size_t cl = 0; cl < C; ++cl)
         for (int k = 0; k < f.nc; ++k) cells[(size_t)fill[hd[cl * f.nc + k]]++] = (int)cl;
     }
+    int mult = 1;
+    for (size_t d = 0; d < (size_t)mc; ++d) mult = std::max(mult, start[d + 1] - start[d]);
+    f.max_mult = mult;
     std::vector<int> cnt(C, 0), owner((size_t)mc, -1);
     for (size_t d = 0; d < (size_t)mc; ++d) {
       int best = -1;
@@ -437,6 +440,7 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
     RC_CUDA(cudaMemcpyAsync(g.dofs.ensure(nd), dofs, nd * sizeof(int), cudaMemcpyDeviceToDevice, c.s));
     RC_CUDA(cudaMemcpyAsync(g.own_pos.ensure(f.own_pos.n), f.own_pos.p, f.own_pos.bytes(), cudaMemcpyDeviceToDevice, c.s));
     g.own_max = f.own_max;
+    g.max_mult = f.max_mult;
     // D^-1 of the embedding: [D^-1; D^-1]
     double* dv = f.Dinv.ensure(2 * mc);
     to_device(c, op->Dinv, dv, mc);

@@ -62,11 +62,13 @@ static void fe_apply_cols(rchfsi_ctx& c, bool useB, const double* X, double* Y, 
   double* xr = c.w.stage_in.ensure((size_t)m * n);
   double* yr = c.w.stage_out.ensure((size_t)m * n);
   transpose_f64(c.s, n, m, X, m, xr, n);  // X col-major = n x m row-major view -> m x n row-major
-  if (c.p.rr_mode == RCHFSI_RR_FP64_EMULATED)
-    fe_apply_f64_rows_tc(c.s, *c.fe, useB, xr, yr, n, c.num_sms);
-  else
+  if (c.p.rr_mode == RCHFSI_RR_FP64_EMULATED) {
+    // the fixed-point accumulator in yr is converted and transposed into Y in one pass
+    fe_apply_f64_rows_tc(c.s, *c.fe, useB, xr, yr, n, c.num_sms, Y);
+  } else {
     fe_apply_f64_rows(c.s, *c.fe, useB, xr, yr, n);
-  transpose_f64(c.s, m, n, yr, n, Y, m);
+    transpose_f64(c.s, m, n, yr, n, Y, m);
+  }
 }
 
 void apply_A_f64(rchfsi_ctx& c, const double* X, double* Y, int n) {

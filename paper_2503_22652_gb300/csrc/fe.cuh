@@ -27,6 +27,7 @@ struct FeOp {
   // does not own it; own_max = the most dofs one cell owns.
   DevBuf<int8_t> own_pos;
   int own_max = 0;
+  int max_mult = 1;              // the most cell listings of one dof (cells sharing it)
   int* err = nullptr;            // device flag raised when a bounded wait in a kernel runs out
   // Complex Hermitian operator A = Ar + i Ai acting on the real embedding [x_r; x_i] of length 2 mc:
   // this object holds Ar (A64) and B, `imag` holds Ai; m = 2 mc, Dinv = [D^-1; D^-1].  Each
@@ -34,18 +35,22 @@ struct FeOp {
   bool cplx = false;
   int64_t mc = 0;
   std::unique_ptr<FeOp> imag;
-  // FP64-accurate tensor-core products (fe_oz.cu): BF16 slice images of the cell matrices (made on
-  // first use) and per-product scratch (column exponents, slice planes of the input block)
+  // FP64-accurate tensor-core products (fe_oz.cu): BF16 slice images of the cell matrices and their
+  // row exponents, per dof the largest exponent of the cell rows that reach it (the scale of its
+  // fixed-point accumulator; made on first use), and per-product scratch (column exponents, slice
+  // planes of the input block)
   mutable DevBuf<uint8_t> ozA, ozB;
-  mutable DevBuf<int> ozAe, ozBe, ozcexp;
+  mutable DevBuf<int> ozAe, ozBe, ozcexp, ozArow, ozBrow;
   mutable DevBuf<__nv_bfloat16> ozplanes;
 };
 
 // Y (row-major m x n) = Op X, Op = A or B, FP64.  Y is overwritten.
 void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n);
-// Same product, FP64-accurate, from exact BF16 slices on the tensor cores (fe_oz.cu).
+// Same product, FP64-accurate, from exact BF16 slices on the tensor cores (fe_oz.cu).  Y (m x n)
+// is the accumulator: with Ycol set, Y is scratch and the product is written column-major to Ycol
+// (leading dimension m); otherwise it is left in Y, row-major.
 void fe_apply_f64_rows_tc(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n,
-                          int num_sms);
+                          int num_sms, double* Ycol = nullptr);
 
 // Filter product for FE operators on row-major m x n blocks, accumulated into Rx (the
 // product-free recurrence terms are applied to Rx beforehand):

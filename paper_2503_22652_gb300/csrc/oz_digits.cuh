@@ -61,4 +61,41 @@ __device__ __forceinline__ double f32_scaled(float x, int p) {
   return __longlong_as_double((long long)bits);
 }
 
+// round(x 2^q) as a signed 64-bit integer (nearest, ties away from zero), by integer arithmetic,
+// for finite x with |x| 2^q < 2^62 and q <= 38 + 150 - (biased exponent of x).  Zero and FP32
+// subnormals give 0.  Branch-free: the 24-bit significand is placed at bit 39 and shifted right
+// by 39 - (its scale), rounding on the bits shifted out.
+__device__ __forceinline__ long long f32_to_fixed(float x, int q) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e8 = (b >> 23) & 0xffu;
+  const int r0 = 189 - (int)e8 - q;  // 39 - (e8 - 150 + q): the right shift
+  // |x| 2^q < 1/2 (r0 > 63) rounds to 0, as does a zero or subnormal x
+  const uint32_t mant = (e8 != 0u && r0 <= 63) ? ((b & 0x7fffffu) | 0x800000u) : 0u;
+  const int r = min(max(r0, 1), 63);
+  unsigned long long u = (unsigned long long)mant << 39;
+  u = (u + (1ull << (r - 1))) >> r;
+  const long long v = (long long)u;
+  return (b >> 31) ? -v : v;
+}
+
+// v 2^e as an FP64 value, rounded to nearest even, by integer arithmetic (|v| < 2^63).
+__device__ __forceinline__ double fixed_to_f64(long long v, int e) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                          // leading one at bit 63
+  unsigned long long mant = a >> 11;  // 53 significant bits
+  const unsigned long long rem = a & 0x7ffull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;
+  long long ex = 63 - lz + (long long)e;  // v 2^e = 1.f 2^ex
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  const long long be = ex + 1023;
+  if (be <= 0 || be >= 2047) return ldexp((double)v, e);  // out of the normal range: rare
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (mant & 0xfffffffffffffull)));
+}
+
 }  // namespace rchfsi

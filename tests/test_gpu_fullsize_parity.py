@@ -101,6 +101,24 @@ def test_fe_filter_6cubed_block600(fe6, prec, N):
         assert err <= FE_LOWP[prec], err
 
 
+@pytest.mark.parametrize("N", [600, 130])
+def test_fe_fp64_products_6cubed(fe6, N):
+    """FP64-accurate FE products (rr_mode "emulated") with more cells than CTAs (several items per
+    CTA, both barrier phases), every 64-column tile of a 600-wide block and a ragged last tile,
+    against the assembled sparse products."""
+    p, A, B = fe6
+    rng = np.random.default_rng(N + 1)
+    X = rng.standard_normal((p["m"], N))
+    L = np.sort(rng.uniform(-20.0, 30.0, N))
+    W = A @ X - (B @ X) * L[None, :]
+    s = Solver(p["m"], nev=N // 2, block=N, rr_mode="emulated")
+    s.set_fe(p["cell_dofs"], p["A_cells"], p["B_cell"], p["Dinv"])
+    Wg, _ = s.residual(X, L)
+    assert relfro(Wg, W) <= 1e-13
+    # the cell contributions are summed in integers: a repeat is bitwise identical
+    assert np.array_equal(s.residual(X, L)[0], Wg)
+
+
 @pytest.fixture(scope="module")
 def kp4():
     p = wl.fe_kpoint_problem(4, (0.15, -0.35, 0.25))     # 64 cells, 4,096 complex dofs
