@@ -991,8 +991,7 @@ int rchfsi_residual(rchfsi_ctx* h, const double* X, const double* Lambda, double
     load_any(c, X, c.w.X.p);
     const std::vector<double> lam = lam_any(c, Lambda);
     RC_CUDA(cudaMemcpyAsync(c.w.evals.p, lam.data(), N * sizeof(double), cudaMemcpyHostToDevice, c.s));
-    apply_A_f64(c, c.w.X.p, c.w.AX.p, N);
-    apply_B_f64(c, c.w.X.p, c.w.BX.p, N);
+    apply_AB_f64(c, c.w.X.p, c.w.AX.p, c.w.BX.p, N);
     resid_form_f64(c.s, m, N, c.w.AX.p, c.w.BX.p, c.w.evals.p, c.w.W.p);
     store_any(c, c.w.W.p, W);
     if (rnorm) {

@@ -56,18 +56,22 @@ static EpiArgs epi_store(void* C, int64_t ldc) {
   return e;
 }
 
-// Row-major <-> column-major for FE applies on column-major solver blocks.
-static void fe_apply_cols(rchfsi_ctx& c, bool useB, const double* X, double* Y, int n) {
+// FE applies on column-major solver blocks: the FP64-accurate tensor-core products take them as
+// they are (both products from one slicing of X); the DFMA path works on row-major copies.
+static void fe_apply_cols(rchfsi_ctx& c, const double* X, double* AX, double* BX, int n) {
   const int64_t m = c.p.m;
-  double* xr = c.w.stage_in.ensure((size_t)m * n);
-  double* yr = c.w.stage_out.ensure((size_t)m * n);
-  transpose_f64(c.s, n, m, X, m, xr, n);  // X col-major = n x m row-major view -> m x n row-major
+  double* s0 = c.w.stage_in.ensure((size_t)m * n);
+  double* s1 = c.w.stage_out.ensure((size_t)m * n);
   if (c.p.rr_mode == RCHFSI_RR_FP64_EMULATED) {
-    // the fixed-point accumulator in yr is converted and transposed into Y in one pass
-    fe_apply_f64_rows_tc(c.s, *c.fe, useB, xr, yr, n, c.num_sms, Y);
-  } else {
-    fe_apply_f64_rows(c.s, *c.fe, useB, xr, yr, n);
-    transpose_f64(c.s, m, n, yr, n, Y, m);
+    fe_apply_f64_cols_tc(c.s, *c.fe, X, AX, BX, n, c.num_sms, s0, s1);
+    return;
+  }
+  transpose_f64(c.s, n, m, X, m, s0, n);  // X col-major = n x m row-major view -> m x n row-major
+  for (int which = 0; which < 2; ++which) {
+    double* out = which ? BX : AX;
+    if (!out) continue;
+    fe_apply_f64_rows(c.s, *c.fe, which == 1, s0, s1, n);
+    transpose_f64(c.s, m, n, s1, n, out, m);
   }
 }
 
@@ -76,7 +80,7 @@ void apply_A_f64(rchfsi_ctx& c, const double* X, double* Y, int n) {
   if (c.op_kind == RCHFSI_OP_DENSE) {
     gemm_f64(c.s, m, n, m, c.dense.A.p, m, true, X, m, true, epi_store(Y, m));
   } else {
-    fe_apply_cols(c, false, X, Y, n);
+    fe_apply_cols(c, X, Y, nullptr, n);
   }
 }
 
@@ -88,7 +92,16 @@ void apply_B_f64(rchfsi_ctx& c, const double* X, double* Y, int n) {
     else
       RC_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, c.s));
   } else {
-    fe_apply_cols(c, true, X, Y, n);
+    fe_apply_cols(c, X, nullptr, Y, n);
+  }
+}
+
+void apply_AB_f64(rchfsi_ctx& c, const double* X, double* AX, double* BX, int n) {
+  if (c.op_kind == RCHFSI_OP_DENSE) {
+    apply_A_f64(c, X, AX, n);
+    apply_B_f64(c, X, BX, n);
+  } else {
+    fe_apply_cols(c, X, AX, BX, n);
   }
 }
 
@@ -824,9 +837,8 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
           RC_CUDA(cudaMemcpyAsync(BY, Y, sizeof(double) * m * N, cudaMemcpyDeviceToDevice, c.s));
         }
       } else {
-        apply_A_f64(c, Y, AY, Na);
+        apply_AB_f64(c, Y, AY, BY, Na);
         jcomplete(AY);
-        apply_B_f64(c, Y, BY, Na);
         jcomplete(BY);
       }
       if (Na != N) oz_slice(c.s, N, m, Y, m, 1, w.ozL);  // every column for the Gram matrices
@@ -837,9 +849,8 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
       oz_slice(c.s, Na, m, BY, m, 1, w.ozR);
       oz_gemm(c.s, c.num_sms, w.ozL, w.ozR, w.GB.p, N, w.ozws, eflag, Na == N);
     } else {
-      apply_A_f64(c, Y, AY, Na);
+      apply_AB_f64(c, Y, AY, BY, Na);
       jcomplete(AY);
-      apply_B_f64(c, Y, BY, Na);
       jcomplete(BY);
       // G_A = Y^T A Y, G_B = Y^T B Y  (N x Na, column-major)
       gemm_f64(c.s, N, Na, m, Y, m, true, AY, m, true, epi_store(w.GA.p, N));
@@ -995,8 +1006,7 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   }
   if (c.rr_paired) jcomplete(X);
   if (direct) {
-    apply_A_f64(c, X, AX, ncol);
-    apply_B_f64(c, X, BX, ncol);
+    apply_AB_f64(c, X, AX, BX, ncol);
     if (c.rr_paired) {
       jcomplete(AX);
       jcomplete(BX);

@@ -46,11 +46,12 @@ struct FeOp {
 
 // Y (row-major m x n) = Op X, Op = A or B, FP64.  Y is overwritten.
 void fe_apply_f64_rows(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n);
-// Same product, FP64-accurate, from exact BF16 slices on the tensor cores (fe_oz.cu).  Y (m x n)
-// is the accumulator: with Ycol set, Y is scratch and the product is written column-major to Ycol
-// (leading dimension m); otherwise it is left in Y, row-major.
-void fe_apply_f64_rows_tc(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n,
-                          int num_sms, double* Ycol = nullptr);
+// AX = A X and/or BX = B X (either output may be null), FP64-accurate, from exact BF16 slices on
+// the tensor cores (fe_oz.cu).  X, AX, BX: column-major m x n, leading dimension m; the slices of X
+// are made once for both products.  accA, accB: m x n scratch blocks (the fixed-point accumulators)
+// for the outputs requested.
+void fe_apply_f64_cols_tc(cudaStream_t s, const FeOp& op, const double* X, double* AX, double* BX, int n,
+                          int num_sms, double* accA, double* accB);
 
 // Filter product for FE operators on row-major m x n blocks, accumulated into Rx (the
 // product-free recurrence terms are applied to Rx beforehand):

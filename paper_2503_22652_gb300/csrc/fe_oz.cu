@@ -108,12 +108,20 @@ __global__ void pack_slices_kernel(int64_t n_cells, int nc, const double* __rest
   }
 }
 
-// Column exponents of a row-major m x n block (max over rows), into cexp (initialised to -100000).
-__global__ void colexp_kernel(int64_t m, int n, const double* __restrict__ X, int* cexp) {
-  for (int j0 = threadIdx.x; j0 < n; j0 += blockDim.x) {
-    int e = -100000;
-    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) e = max(e, exp_of(X[i * n + j0]));
-    if (e > -100000) atomicMax(cexp + j0, e);
+// Column exponents of a column-major m x n block X (leading dimension m): one block per column,
+// cexp[j] = the largest exponent in column j (-100000 for a zero column).
+__global__ void __launch_bounds__(256) colexp_cols_kernel(int64_t m, const double* __restrict__ X, int* cexp) {
+  __shared__ int red[8];
+  const double* col = X + (int64_t)blockIdx.x * m;
+  int e = -100000;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) e = max(e, exp_of(col[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
+    cexp[blockIdx.x] = e;
   }
 }
 
@@ -165,41 +173,36 @@ __global__ void __launch_bounds__(256) fixed_to_cols_kernel(int64_t m, int n, in
   }
 }
 
-// Same conversion in place, row-major (the int64 and FP64 entries share their storage).
-__global__ void fixed_to_rows_kernel(int64_t m, int n, int64_t mrow, long long* V, const int* __restrict__ rowexp,
-                                     const int* __restrict__ cexp, int H) {
-  const int64_t total = m * (int64_t)n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n;
-    const int j = (int)(e % n);
-    const double v = fixed_value(V[e], rowexp[i < mrow ? i : i - mrow], cexp[j], H);
-    reinterpret_cast<double*>(V)[e] = v;
+// The 7 slice planes of a column-major m x n block X (leading dimension m): plane t holds the
+// digits u_t as BF16, row-major with np >= n columns (np a multiple of 64, columns n .. np-1 zero),
+// so that every dof row of a column tile is one aligned 128-byte run.  32 x 32 tiles through shared
+// memory: reads coalesced along the rows of X, writes along the columns of the planes.
+__global__ void __launch_bounds__(256) xslice_cols_kernel(int64_t m, int n, int np, const double* __restrict__ X,
+                                                          const int* __restrict__ cexp,
+                                                          __nv_bfloat16* __restrict__ planes) {
+  __shared__ double tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int c = ty; c < 32; c += 8) {
+    const int j = j0 + c;
+    const int64_t i = i0 + tx;
+    tile[c][tx] = (j < n && i < m) ? X[(int64_t)j * m + i] : 0.0;
   }
-}
-
-// The 7 slice planes of X (row-major m x n): plane t holds the digits u_t as BF16, row-major with
-// np >= n columns (np a multiple of 64, columns n .. np-1 zero), so that every dof row of a column
-// tile is one aligned 128-byte run.  Thread (x, y): column pair 2x of rows y, y + gridDim.y
-// blockDim.y, ... (the column exponents are loaded once; 4-byte stores per plane).
-__global__ void __launch_bounds__(256) xslice_kernel(int64_t m, int n, int np, const double* __restrict__ X,
-                                                     const int* __restrict__ cexp,
-                                                     __nv_bfloat16* __restrict__ planes) {
-  const int j = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (j >= np) return;
-  const bool in0 = j < n, in1 = j + 1 < n;
-  int e0 = in0 ? cexp[j] : 0, e1 = in1 ? cexp[j + 1] : 0;
-  if (e0 == -100000) e0 = 0;
-  if (e1 == -100000) e1 = 0;
+  __syncthreads();
+  const int j = j0 + tx;
+  int e = (j < n) ? cexp[j] : 0;
+  if (e == -100000) e = 0;
   const int64_t pstride = m * (int64_t)np;
-  for (int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; i < m; i += (int64_t)gridDim.y * blockDim.y) {
-    long long f0 = in0 ? fixed56(X[i * n + j], e0) : 0;
-    long long f1 = in1 ? fixed56(X[i * n + j + 1], e1) : 0;
-    const int64_t e = i * np + j;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r;
+    if (i >= m) break;
+    long long f = fixed56(tile[tx][r], e);
+    __nv_bfloat16* dst = planes + i * np + j;
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       // |digit| <= 256: converted through int (a 64-bit integer conversion uses the FP64 pipe)
-      const float d0 = (float)(int)next_digit(f0, t), d1 = (float)(int)next_digit(f1, t);
-      *reinterpret_cast<__nv_bfloat162*>(planes + (int64_t)t * pstride + e) = __floats2bfloat162_rn(d0, d1);
+      dst[(int64_t)t * pstride] = __float2bfloat16_rn((float)(int)next_digit(f, t));
     }
   }
 }
@@ -647,57 +650,52 @@ void launch_oz(cudaStream_t s, int num_sms, const FeOp& op, bool useB, const __n
 
 }  // namespace
 
-void fe_apply_f64_rows_tc(cudaStream_t s, const FeOp& op, bool useB, const double* X, double* Y, int n,
-                          int num_sms, double* Ycol) {
+void fe_apply_f64_cols_tc(cudaStream_t s, const FeOp& op, const double* X, double* AX, double* BX, int n,
+                          int num_sms, double* accA, double* accB) {
   RC_CHECK(op.nc <= kNCP, RCHFSI_ERR_INVALID_ARG, "n_c larger than 128");
+  RC_CHECK((!AX || accA) && (!BX || accB), RCHFSI_ERR_INVALID_ARG, "fixed-point accumulator missing");
   const int64_t m = op.m;
-  if (n <= 0 || m <= 0) return;
-  // fixed-point accumulator (64-bit integers in Y's storage), zero
-  long long* V = reinterpret_cast<long long*>(Y);
-  RC_CUDA(cudaMemsetAsync(V, 0, sizeof(long long) * m * n, s));
-  const int* rowexp = ensure_rowexp(s, op, useB);
-  const int H = headroom(op, useB);
-  // column exponents over every row (both halves of a complex block), then the slice planes,
-  // rows padded to np columns
+  if (n <= 0 || m <= 0 || (!AX && !BX)) return;
+  // column exponents over every row (both halves of a complex block), then the slice planes of
+  // X, rows padded to np columns: made once for both products
   int* cexp = op.ozcexp.ensure(n);
-  fill_int(s, cexp, n, -100000);
-  colexp_kernel<<<(unsigned)std::min<int64_t>(m, 152 * 8), 256, 0, s>>>(m, n, X, cexp);
+  colexp_cols_kernel<<<(unsigned)n, 256, 0, s>>>(m, X, cexp);
   RC_LAUNCH();
   const int np = (int)cdiv(n, kBN) * kBN;
   const int64_t total = m * (int64_t)np;
   __nv_bfloat16* planes = op.ozplanes.ensure((size_t)S * total);
-  {
-    // 32 column pairs x 8 rows per block; enough row blocks for ~16 blocks per SM
-    const unsigned gx = cdiv(np / 2, 32);
-    const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(m, 8), (int64_t)num_sms * 16 / gx + 1));
-    xslice_kernel<<<dim3(gx, gy), dim3(32, 8), 0, s>>>(m, n, np, X, cexp, planes);
+  xslice_cols_kernel<<<dim3(cdiv(m, 32), (unsigned)(np / 32)), 256, 0, s>>>(m, n, np, X, cexp, planes);
+  RC_LAUNCH();
+  const int64_t mrow = op.cplx ? op.mc : m;
+  for (int which = 0; which < 2; ++which) {
+    const bool useB = which == 1;
+    double* out = useB ? BX : AX;
+    if (!out) continue;
+    // fixed-point accumulator (64-bit integers in the scratch block), zero
+    long long* V = reinterpret_cast<long long*>(useB ? accB : accA);
+    RC_CUDA(cudaMemsetAsync(V, 0, sizeof(long long) * m * n, s));
+    const int* rowexp = ensure_rowexp(s, op, useB);
+    const int H = headroom(op, useB);
+    if (!op.cplx) {
+      launch_oz(s, num_sms, op, useB, planes, total, np, rowexp, H, V, n, false);
+    } else {
+      // complex operator on the real embedding (rows [0, mc) real parts, [mc, 2 mc) imaginary
+      // parts): Y_r = Ar X_r - Ai X_i,  Y_i = Ai X_r + Ar X_i;  the real B acts on each half
+      const int64_t poff = op.mc * (int64_t)np, yoff = op.mc * (int64_t)n;
+      if (useB) {
+        launch_oz(s, num_sms, op, true, planes, total, np, rowexp, H, V, n, false);
+        launch_oz(s, num_sms, op, true, planes + poff, total, np, rowexp, H, V + yoff, n, false);
+      } else {
+        const FeOp& im = *op.imag;
+        launch_oz(s, num_sms, op, false, planes, total, np, rowexp, H, V, n, false);
+        launch_oz(s, num_sms, im, false, planes + poff, total, np, rowexp, H, V, n, true);
+        launch_oz(s, num_sms, im, false, planes, total, np, rowexp, H, V + yoff, n, false);
+        launch_oz(s, num_sms, op, false, planes + poff, total, np, rowexp, H, V + yoff, n, false);
+      }
+    }
+    fixed_to_cols_kernel<<<dim3(cdiv(m, 32), cdiv(n, 32)), 256, 0, s>>>(m, n, mrow, V, rowexp, cexp, H, out);
     RC_LAUNCH();
   }
-  if (!op.cplx) {
-    launch_oz(s, num_sms, op, useB, planes, total, np, rowexp, H, V, n, false);
-  } else {
-    // complex operator on the real embedding (rows [0, mc) real parts, [mc, 2 mc) imaginary parts):
-    //   Y_r = Ar X_r - Ai X_i,  Y_i = Ai X_r + Ar X_i;  the real B acts on each half
-    const int64_t poff = op.mc * (int64_t)np, yoff = op.mc * (int64_t)n;
-    if (useB) {
-      launch_oz(s, num_sms, op, true, planes, total, np, rowexp, H, V, n, false);
-      launch_oz(s, num_sms, op, true, planes + poff, total, np, rowexp, H, V + yoff, n, false);
-    } else {
-      const FeOp& im = *op.imag;
-      launch_oz(s, num_sms, op, false, planes, total, np, rowexp, H, V, n, false);
-      launch_oz(s, num_sms, im, false, planes + poff, total, np, rowexp, H, V, n, true);
-      launch_oz(s, num_sms, im, false, planes, total, np, rowexp, H, V + yoff, n, false);
-      launch_oz(s, num_sms, op, false, planes + poff, total, np, rowexp, H, V + yoff, n, false);
-    }
-  }
-  const int64_t mrow = op.cplx ? op.mc : m;
-  if (Ycol) {
-    fixed_to_cols_kernel<<<dim3(cdiv(m, 32), cdiv(n, 32)), 256, 0, s>>>(m, n, mrow, V, rowexp, cexp, H, Ycol);
-  } else {
-    fixed_to_rows_kernel<<<(unsigned)std::min<int64_t>(cdiv(m * n, 256), 152 * 16), 256, 0, s>>>(m, n, mrow, V,
-                                                                                                 rowexp, cexp, H);
-  }
-  RC_LAUNCH();
 }
 
 }  // namespace rchfsi

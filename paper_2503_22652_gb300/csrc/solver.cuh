@@ -89,6 +89,7 @@ namespace rchfsi {
 // Operator applications in FP64 on column-major m x n blocks.
 void apply_A_f64(rchfsi_ctx& c, const double* X, double* Y, int n);
 void apply_B_f64(rchfsi_ctx& c, const double* X, double* Y, int n);  // Y = B X (copy when B = I)
+void apply_AB_f64(rchfsi_ctx& c, const double* X, double* AX, double* BX, int n);  // both, one pass over X
 bool has_B(const rchfsi_ctx& c);
 const double* dinv_diag(const rchfsi_ctx& c);
 
