@@ -395,10 +395,10 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
   const size_t blk = (size_t)m * N;
   const int prec = c.p.precision;
   FeOp& f = *c.fe;
-  // row-major working copy of the input block (W for Algorithm 3, X for Algorithm 2)
-  double* Wr = c.w.stage_out.ensure(blk);
-  transpose_f64(c.s, N, m, chfsi ? X : W, m, Wr, N);
   if (prec == RCHFSI_FP64) {
+    // row-major working copy of the input block (W for Algorithm 3, X for Algorithm 2)
+    double* Wr = c.w.stage_out.ensure(blk);
+    transpose_f64(c.s, N, m, chfsi ? X : W, m, Wr, N);
     double* RX = c.w.AY.p;
     double* RY = c.w.BY.p;
     if (!chfsi) {
@@ -431,9 +431,9 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
     float* RY = c.w.R32b.ensure(blk);
     float* Wl = c.w.W32.ensure(blk);
     check_budget(c);
-    cast_f64_to_f32(c.s, blk, Wr, RY, s1 / e, 0);  // S_1 = R_1 = (sigma_1 / e) W
-    cast_f64_to_f32(c.s, blk, Wr, Wl, 1.0, 0);
-    fill_zero(c.s, RX, blk * sizeof(float));       // S_0 = R_0 = 0
+    // S_1 = R_1 = (sigma_1 / e) W and W, row-major FP32, in one pass over the column-major W
+    cols_to_rows_f32x2(c.s, m, N, W, s1 / e, 1.0, RY, Wl);
+    fill_zero(c.s, RX, blk * sizeof(float));  // S_0 = R_0 = 0
     if (!co.empty()) {
       float* lamf = c.w.lamtab_f.ensure((size_t)(p + 1) * N);  // the Lambda table in FP32 for the kernel
       cast_f64_to_f32(c.s, (int64_t)(p + 1) * N, lamtab, lamf, 1.0, 0);
@@ -448,9 +448,8 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
         std::swap(RX, RY);
       }
     }
-    cast_f32_to_f64(c.s, blk, RY, Wr, 1.0 / sc[p]);  // R_p = S_p / s_p
-    transpose_f64(c.s, m, N, Wr, N, Y, m);
-    reconstruct_f64(c.s, m, N, Y, m, f.Dinv.p, X, lamtab + (size_t)p * N, Y);
+    // Y = D^-1 R_p + X Lambda_p with R_p = S_p / s_p, in one pass back to column-major
+    rows_to_cols_recon(c.s, m, N, RY, 1.0 / sc[p], f.Dinv.p, X, lamtab + (size_t)p * N, Y);
     c.last_applies = (int64_t)co.size();
     return;
   }
@@ -459,10 +458,9 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
   float* Wl = c.w.W32.ensure(blk);
   check_budget(c);
   if (!chfsi) {
-    cast_f64_to_f32(c.s, blk, Wr, RY, s1 / e, 0);
-    cast_f64_to_f32(c.s, blk, Wr, Wl, 1.0, 0);
+    cols_to_rows_f32x2(c.s, m, N, W, s1 / e, 1.0, RY, Wl);
   } else {
-    cast_f64_to_f32(c.s, blk, Wr, RX, 1.0, 0);
+    cols_to_rows_f32x2(c.s, m, N, X, 1.0, 1.0, RX, RX);
     recur_terms_rows_f32(c.s, m, N, RX, RY, nullptr, nullptr, 0.0, -(s1 / e) * cc, 0.0);
     fe_filter_product_f32(c.s, f, prec, RX, RY, N, (float)(s1 / e), 2);
   }
@@ -473,9 +471,8 @@ static void filter_fe(rchfsi_ctx& c, const double* X, const double* W, int p, co
     fe_filter_product_f32(c.s, f, prec, RY, RX, N, (float)co[k].a, chfsi ? 2 : 1);
     std::swap(RX, RY);
   }
-  cast_f32_to_f64(c.s, blk, RY, Wr);
-  transpose_f64(c.s, m, N, Wr, N, Y, m);
-  if (!chfsi) reconstruct_f64(c.s, m, N, Y, m, f.Dinv.p, X, lamtab + (size_t)p * N, Y);
+  // Y = D^-1 R_p + X Lambda_p (Algorithm 3), or Y = R_p (Algorithm 2: no D^-1, zero Lambda)
+  rows_to_cols_recon(c.s, m, N, RY, 1.0, chfsi ? nullptr : f.Dinv.p, X, chfsi ? c.w.nrm.p : lamtab + (size_t)p * N, Y);
   c.last_applies = (int64_t)co.size() + (chfsi ? 1 : 0);
 }
 
@@ -630,10 +627,7 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     RX[q] = c.w.R32a.ensure(blk);
     RY[q] = c.w.R32b.ensure(blk);
     WL[q] = c.w.W32.ensure(blk);
-    double* Wr = c.w.stage_out.ensure(blk);
-    transpose_f64(s, n, m, J.W, m, Wr, n);
-    cast_f64_to_f32(s, blk, Wr, RY[q], s1 / e, 0);
-    cast_f64_to_f32(s, blk, Wr, WL[q], 1.0, 0);
+    cols_to_rows_f32x2(s, m, n, J.W, s1 / e, 1.0, RY[q], WL[q]);
     fill_zero(s, RX[q], blk * sizeof(float));
     if (fused) {
       fe_step_prepare(s, *c.fe);
@@ -746,12 +740,10 @@ void filter_fe_batch(cudaStream_t s, int num_sms, std::vector<FeFilterJob>& jobs
     rchfsi_ctx& c = *J.c;
     const int n = nn[q];
     const int64_t m = c.p.m;
-    const size_t blk = (size_t)m * n;
     float* ryf = ((p - 1) % 2 == 0) ? RY[q] : RX[q];
-    double* Wr = c.w.stage_out.p;
-    cast_f32_to_f64(s, blk, ryf, Wr, fused ? 1.0 / scales[q][p] : 1.0);  // fused: R_p = S_p / s_p
-    transpose_f64(s, m, n, Wr, n, J.Y, m);
-    reconstruct_f64(s, m, n, J.Y, m, c.fe->Dinv.p, J.X, dtab[q] + (size_t)p * n, J.Y);
+    // fused: R_p = S_p / s_p
+    rows_to_cols_recon(s, m, n, ryf, fused ? 1.0 / scales[q][p] : 1.0, c.fe->Dinv.p, J.X, dtab[q] + (size_t)p * n,
+                       J.Y);
     if (c.cplx) cplx_rebuild(s, c.mc, c.Nc, J.Y, nullptr, J.Y);
     c.last_applies = p - 1;
     c.last_flops = 2.0 * c.fe->nc * c.fe->nc * (double)c.fe->n_cells * n * (c.fe->cplx ? 4.0 : 1.0) * (p - 1);

@@ -131,6 +131,12 @@ void scale_cols_f64(cudaStream_t s, int64_t m, int64_t n, double* X, int64_t ld,
 void col_norms_f64(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_t ld, double* out);
 void scale_rows_f64(cudaStream_t s, int64_t m, int64_t n, const double* in, double* out, const double* d,
                     bool cols);  // out = diag(d)*in (cols=false) or in*diag(d) (cols=true); row-major m x n
+// o1 = (float)(s1 W), o2 = (float)(s2 W) as row-major m x n blocks, W column-major (leading dim m)
+void cols_to_rows_f32x2(cudaStream_t s, int64_t m, int64_t n, const double* W, double s1, double s2, float* o1,
+                        float* o2);
+// Y = dinv .* (rs R) + X diag(lam), R row-major float m x n, X and Y column-major (leading dim m)
+void rows_to_cols_recon(cudaStream_t s, int64_t m, int64_t n, const float* R, double rs, const double* dinv,
+                        const double* X, const double* lam, double* Y);
 void cast_f64_to_f32(cudaStream_t s, int64_t n, const double* in, float* out, double scale, int round_tf32);
 void cast_f64_to_bf16(cudaStream_t s, int64_t n, const double* in, __nv_bfloat16* out, double scale);
 void cast_f32_to_f64(cudaStream_t s, int64_t n, const float* in, double* out, double scale = 1.0);

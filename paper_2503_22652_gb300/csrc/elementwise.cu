@@ -30,6 +30,53 @@ __global__ void transpose_kernel(int64_t rows, int64_t cols, const double* __res
   }
 }
 
+// o1(i, j) = (float)(W(i, j) s1), o2(i, j) = (float)(W(i, j) s2): W column-major (leading dimension
+// m), o1 and o2 row-major m x n.  32 x 32 shared-memory tiles, rows on blockIdx.x.
+__global__ void __launch_bounds__(256) cols_to_rows_f32x2_kernel(int64_t m, int64_t n, const double* __restrict__ W,
+                                                                 double s1, double s2, float* __restrict__ o1,
+                                                                 float* __restrict__ o2) {
+  __shared__ double t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int c = ty; c < 32; c += 8) {
+    const int64_t i = i0 + tx, j = j0 + c;
+    t[c][tx] = (i < m && j < n) ? W[j * m + i] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + tx;
+    if (i < m && j < n) {
+      const double w = t[tx][r];
+      o1[i * n + j] = (float)(w * s1);
+      o2[i * n + j] = (float)(w * s2);
+    }
+  }
+}
+
+// Y(i, j) = dinv[i] (rs R(i, j)) + X(i, j) lam[j] (dinv optional): R row-major float (leading
+// dimension n); X and Y column-major (leading dimension m).  32 x 32 shared-memory tiles.
+__global__ void __launch_bounds__(256) rows_to_cols_recon_kernel(int64_t m, int64_t n, const float* __restrict__ R,
+                                                                 double rs, const double* __restrict__ dinv,
+                                                                 const double* X, const double* __restrict__ lam,
+                                                                 double* Y) {
+  __shared__ double t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + tx;
+    t[r][tx] = (i < m && j < n) ? rs * (double)R[i * n + j] : 0.0;
+  }
+  __syncthreads();
+  for (int c = ty; c < 32; c += 8) {
+    const int64_t i = i0 + tx, j = j0 + c;
+    if (i < m && j < n) {
+      double v = t[tx][c];
+      if (dinv) v *= dinv[i];
+      Y[j * m + i] = fma(X[j * m + i], lam[j], v);
+    }
+  }
+}
+
 __global__ void scale_cols_kernel(int64_t m, int64_t n, double* X, int64_t ld, const double* scale) {
   const int64_t total = m * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += grid_threads()) {
@@ -203,6 +250,22 @@ void col_norms_f64(cudaStream_t s, int64_t m, int64_t n, const double* X, int64_
 void scale_rows_f64(cudaStream_t s, int64_t m, int64_t n, const double* in, double* out, const double* d,
                     bool cols) {
   scale_rows_kernel<<<ew_blocks(m * n), 256, 0, s>>>(m, n, in, out, d, cols ? 1 : 0);
+  RC_LAUNCH();
+}
+
+void cols_to_rows_f32x2(cudaStream_t s, int64_t m, int64_t n, const double* W, double s1, double s2, float* o1,
+                        float* o2) {
+  if (m <= 0 || n <= 0) return;
+  RC_CHECK(cdiv(n, 32) <= 65535u, RCHFSI_ERR_INVALID_ARG, "cols_to_rows: too many columns for the grid");
+  cols_to_rows_f32x2_kernel<<<dim3(cdiv(m, 32), cdiv(n, 32)), 256, 0, s>>>(m, n, W, s1, s2, o1, o2);
+  RC_LAUNCH();
+}
+
+void rows_to_cols_recon(cudaStream_t s, int64_t m, int64_t n, const float* R, double rs, const double* dinv,
+                        const double* X, const double* lam, double* Y) {
+  if (m <= 0 || n <= 0) return;
+  RC_CHECK(cdiv(n, 32) <= 65535u, RCHFSI_ERR_INVALID_ARG, "rows_to_cols: too many columns for the grid");
+  rows_to_cols_recon_kernel<<<dim3(cdiv(m, 32), cdiv(n, 32)), 256, 0, s>>>(m, n, R, rs, dinv, X, lam, Y);
   RC_LAUNCH();
 }
 

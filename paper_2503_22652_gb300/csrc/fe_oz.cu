@@ -659,13 +659,16 @@ void fe_apply_f64_cols_tc(cudaStream_t s, const FeOp& op, const double* X, doubl
   // column exponents over every row (both halves of a complex block), then the slice planes of
   // X, rows padded to np columns: made once for both products
   int* cexp = op.ozcexp.ensure(n);
-  colexp_cols_kernel<<<(unsigned)n, 256, 0, s>>>(m, X, cexp);
-  RC_LAUNCH();
   const int np = (int)cdiv(n, kBN) * kBN;
   const int64_t total = m * (int64_t)np;
   __nv_bfloat16* planes = op.ozplanes.ensure((size_t)S * total);
-  xslice_cols_kernel<<<dim3(cdiv(m, 32), (unsigned)(np / 32)), 256, 0, s>>>(m, n, np, X, cexp, planes);
-  RC_LAUNCH();
+  {
+    prof::Scope ps(s, RCHFSI_KERNEL_RR_AUX, 0.0, 16.0 * m * n + 14.0 * (double)total);
+    colexp_cols_kernel<<<(unsigned)n, 256, 0, s>>>(m, X, cexp);
+    RC_LAUNCH();
+    xslice_cols_kernel<<<dim3(cdiv(m, 32), (unsigned)(np / 32)), 256, 0, s>>>(m, n, np, X, cexp, planes);
+    RC_LAUNCH();
+  }
   const int64_t mrow = op.cplx ? op.mc : m;
   for (int which = 0; which < 2; ++which) {
     const bool useB = which == 1;
@@ -693,6 +696,7 @@ void fe_apply_f64_cols_tc(cudaStream_t s, const FeOp& op, const double* X, doubl
         launch_oz(s, num_sms, op, false, planes + poff, total, np, rowexp, H, V + yoff, n, false);
       }
     }
+    prof::Scope ps(s, RCHFSI_KERNEL_RR_AUX, 0.0, 16.0 * m * n);
     fixed_to_cols_kernel<<<dim3(cdiv(m, 32), cdiv(n, 32)), 256, 0, s>>>(m, n, mrow, V, rowexp, cexp, H, out);
     RC_LAUNCH();
   }
