@@ -889,12 +889,21 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
     c.rr_retries = 1;
   }
   if (info != 0) return RCHFSI_ERR_ILL_CONDITIONED;
-  // M = L^-1 G_A L^-T (two FP64 GEMMs on all SMs)
-  {
+  // M = L^-1 G_A L^-T: two FP64-accurate products (BF16 slices on the tensor cores, the Gram
+  // slices no longer needed) or two FP64 GEMMs on all SMs
+  if (emu) {
+    oz_slice(c.s, N, N, w.Li.p, 1, N, w.ozR);   // L^-1, row i = L^-1(i, :)
+    oz_slice(c.s, N, N, w.GA.p, N, 1, w.ozE);   // column j of G_A as row j
+    oz_gemm(c.s, c.num_sms, w.ozR, w.ozE, w.Zt.p, N, w.ozws, eflag);
+    oz_slice(c.s, N, N, w.Zt.p, 1, N, w.ozE);   // L^-1 G_A by rows
+    oz_gemm(c.s, c.num_sms, w.ozE, w.ozR, w.Z.p, N, w.ozws, eflag);
+  } else {
     EpiArgs e1 = epi_store(w.Zt.p, N), e2 = epi_store(w.Z.p, N);
     e1.prof_cls = e2.prof_cls = RCHFSI_KERNEL_SMALL_DENSE;
     gemm_f64(c.s, N, N, N, w.Li.p, N, false, w.GA.p, N, true, e1);
     gemm_f64(c.s, N, N, N, w.Zt.p, N, false, w.Li.p, N, false, e2);
+  }
+  {
     prof::Scope ps(c.s, RCHFSI_KERNEL_SMALL_DENSE, 0.0, 8.0 * N * N * 2);
     symmetrize_f64(c.s, N, w.Z.p, N);
   }
@@ -920,7 +929,11 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
   }
   // E = L^-T V
   double* Ep = vec == w.Z.p ? w.Zt.p : w.Z.p;
-  {
+  if (emu) {
+    oz_slice(c.s, N, N, w.Li.p, N, 1, w.ozR);  // L^-T, row i = column i of L^-1
+    oz_slice(c.s, N, N, vec, N, 1, w.ozE);     // column j of V as row j
+    oz_gemm(c.s, c.num_sms, w.ozR, w.ozE, Ep, N, w.ozws, eflag);
+  } else {
     EpiArgs e3 = epi_store(Ep, N);
     e3.prof_cls = RCHFSI_KERNEL_SMALL_DENSE;
     gemm_f64(c.s, N, N, N, w.Li.p, N, true, vec, N, true, e3);
