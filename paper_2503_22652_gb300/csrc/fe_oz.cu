@@ -278,7 +278,9 @@ __device__ __forceinline__ uint32_t x_par(int t, int64_t j) { return (uint32_t)(
 
 __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constant__ FeOzArgs p) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t afull[kARing], aempty[kARing], xfull[8], xempty[8], lev[S], bfree[8], mdone;
+  // lev[j & 1][L]: level L of item j has all its products (two sets, so that the next item's levels
+  // never complete a phase that the epilogue is still waiting for)
+  __shared__ __align__(8) uint64_t afull[kARing], aempty[kARing], xfull[8], xempty[8], lev[2][S], bfree[8], mdone;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -295,7 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
       tc::mbar_init(&xempty[b], 1);
       tc::mbar_init(&bfree[b], 512);  // every epilogue thread, once it has read the block
     }
-    for (int t = 0; t < S; ++t) tc::mbar_init(&lev[t], 1);
+    for (int t = 0; t < S; ++t) {
+      tc::mbar_init(&lev[0][t], 1);
+      tc::mbar_init(&lev[1][t], 1);
+    }
     tc::mbar_init(&mdone, 1);
     tc::fence_barrier_init();
     abort_flag = 0;
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
           tc::mma_commit(&aempty[q]);
           // level s has all its products, and X slice 6 - s is not read again (for slices 1..6
           // the gather waits on lev[] itself)
-          tc::mma_commit(&lev[s]);
+          tc::mma_commit(&lev[j & 1][s]);
           if (s == S - 1) tc::mma_commit(&xempty[x_block(0, j)]);
         }
         __syncwarp();
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
         const int b = x_block(t, j);
         // slice t >= 1 is free once pass 6 - t of the previous item is done; slice 0's block once
         // the item before that is done
-        const bool freed = t ? (j == 0 || tc::mbar_wait(&lev[S - 1 - t], (uint32_t)((j - 1) & 1)))
+        const bool freed = t ? (j == 0 || tc::mbar_wait(&lev[(j - 1) & 1][S - 1 - t], (uint32_t)(((j - 1) >> 1) & 1)))
                              : tc::mbar_wait(&xempty[b], x_par(0, j) ^ 1u);
         if (*vabort || !freed) {
           ok = false;
@@ -481,7 +486,8 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
     for (int64_t j = 0; j < items; ++j) {
       const int64_t cell = blockIdx.x + (j / p.ntiles) * G;
       const int tile = (int)(j % p.ntiles);
-      const uint32_t par = (uint32_t)(j & 1);
+      uint64_t* lv = lev[j & 1];
+      const uint32_t par = (uint32_t)((j >> 1) & 1);
       int g = -1, qs = 0;
       if (i < p.nc) {
         g = __ldg(p.dofs + cell * p.nc + i);
@@ -495,23 +501,15 @@ __global__ void __launch_bounds__(kThreads, 1) fe_oz_kernel(const __grid_constan
       float scale = 1.f;
 #pragma unroll 1
       for (int L = 0; L < S; ++L) {
-        const bool w = !*vabort && tc::mbar_wait(&lev[L], par);
+        const bool w = !*vabort && tc::mbar_wait(&lv[L], par);
         ok = __all_sync(0xffffffffu, w);
         if (!ok) break;
         tc::tc_fence_after();
-        if (L == S - 1) {
-          // level 5's block is released only now: the next item cannot then complete any level
-          // before this item's last one has been waited for (one phase of lev[] in flight)
-          tc::tc_fence_before();
-          tc::mbar_arrive(&bfree[perm_block(perm, S - 2)]);
-        }
         const uint32_t blk = perm_block(perm, L);
         float v[16];
         tc::tmem_ld16(lane_base + blk * (uint32_t)kBN, v);
-        if (L != S - 2) {
-          tc::tc_fence_before();
-          tc::mbar_arrive(&bfree[blk]);
-        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&bfree[blk]);
         if (L == 0) {
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
