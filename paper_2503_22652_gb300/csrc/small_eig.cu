@@ -282,6 +282,185 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(int n, const double*
   }
 }
 
+// ------------------------------------------------------------------ blocked Cholesky and L^-1
+// A = L L^T (A symmetric positive definite, n x n column-major, lower triangle read) and L^-1, on a
+// cooperative grid, in 32 x 32 tiles: per block column K, one CTA factors the diagonal tile and
+// inverts its factor (DI_K), all CTAs solve the panel L_IK = A_IK DI_K^T and update the trailing
+// lower triangle A_IJ -= L_IK L_JK^T; then L^-1 by the right-looking block forward substitution of
+// L X = I: X_K,: = DI_K B_K,: and B_I,: -= L_IK X_K,: for I > K.  5 grid barriers per block column
+// instead of one per column, and the FP64 work spread over every SM.
+// di: scratch of ceil(n / 32) x 32 x 32 doubles; bad: one int of scratch.  info: 0, or j + 1 for the
+// first column j whose pivot is not positive (L and L^-1 are then not written in full).
+constexpr int CB = 32;
+
+// C(32 x 32 tile in shared memory, row-major stride 33) (+|-)= A B^T or A B, the tiles staged in
+// shared memory; 256 threads, 4 outputs each (rows ty + 8 u, column tx).
+__device__ __forceinline__ void tile_acc(double (*C)[CB + 1], const double (*A)[CB + 1], const double (*B)[CB + 1],
+                                         bool btrans, double sign) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+  for (int k = 0; k < CB; ++k) {
+    const double b = btrans ? B[tx][k] : B[k][tx];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(A[ty + 8 * u][k], b, acc[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) C[ty + 8 * u][tx] = fma(sign, acc[u], C[ty + 8 * u][tx]);
+}
+
+// Tile (I, J) of a column-major n x n matrix to / from shared memory (zeros outside the matrix).
+__device__ __forceinline__ void tile_load(double (*T)[CB + 1], const double* M, int n, int I, int J) {
+  for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+    const int c = e / CB, r = e % CB, i = I * CB + r, j = J * CB + c;
+    T[r][c] = (i < n && j < n) ? __ldcg(M + (size_t)j * n + i) : 0.0;
+  }
+}
+__device__ __forceinline__ void tile_store(const double (*T)[CB + 1], double* M, int n, int I, int J) {
+  for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+    const int c = e / CB, r = e % CB, i = I * CB + r, j = J * CB + c;
+    if (i < n && j < n) __stcg(M + (size_t)j * n + i, T[r][c]);
+  }
+}
+
+__global__ void __launch_bounds__(256) chol_inv_blocked_kernel(int n, const double* __restrict__ A, double* L,
+                                                               double* Linv, double* di, int* bad, int* info) {
+  __shared__ double T0[CB][CB + 1], T1[CB][CB + 1], T2[CB][CB + 1];
+  __shared__ double rdiag[CB];  // 1 / L_jj of the diagonal tile
+  cg::grid_group grid = cg::this_grid();
+  const int P = gridDim.x, r = blockIdx.x, tid = threadIdx.x;
+  const int nt = (n + CB - 1) / CB;
+  const size_t nn = (size_t)n * n;
+  // L = lower(A), Linv = I
+  for (size_t e = (size_t)r * blockDim.x + tid; e < nn; e += (size_t)P * blockDim.x) {
+    const size_t j = e / n, i = e - j * n;
+    __stcg(L + e, i >= j ? A[e] : 0.0);
+    __stcg(Linv + e, i == j ? 1.0 : 0.0);
+  }
+  if (r == 0 && tid == 0) *bad = 0;
+  grid.sync();
+  for (int K = 0; K < nt; ++K) {
+    const int nb = min(CB, n - K * CB);
+    // ---- diagonal tile: Cholesky in shared memory, then DI_K = L_KK^-1 (CTA 0)
+    if (r == 0) {
+      tile_load(T0, L, n, K, K);
+      __syncthreads();
+      for (int j = 0; j < nb; ++j) {
+        const double d = T0[j][j];
+        if (!(d > 0.0) || !isfinite(d)) {
+          if (tid == 0) {
+            *bad = K * CB + j + 1;
+            *info = K * CB + j + 1;
+          }
+          break;
+        }
+        const double inv = rsqrt(d);
+        if (tid == 0) rdiag[j] = inv;
+        __syncthreads();
+        if (tid > j && tid < nb) T0[tid][j] *= inv;
+        __syncthreads();
+        // trailing update inside the tile: T0[i][k] -= T0[i][j] T0[k][j], j < k <= i < nb
+        for (int e = tid; e < CB * CB; e += blockDim.x) {
+          const int i = e / CB, k = e % CB;
+          if (k > j && k <= i && i < nb) T0[i][k] = fma(-T0[i][j], T0[k][j], T0[i][k]);
+        }
+        if (tid == 0) T0[j][j] = d * inv;
+        __syncthreads();
+      }
+      // the update also wrote the tile's upper half: L is lower triangular
+      for (int e = tid; e < CB * CB; e += blockDim.x)
+        if (e % CB > e / CB) T0[e / CB][e % CB] = 0.0;
+      __syncthreads();
+      if (*(volatile int*)bad == 0) {
+        // DI = L_KK^-1 by forward substitution, 8 threads per column c: x_i = (delta_ic - sum_k
+        // L_ik x_k) / L_ii for i >= c, the sum split over the 8 threads
+        const int c = tid >> 3, s = tid & 7;
+        for (int e = tid; e < CB * CB; e += blockDim.x) T1[e / CB][e % CB] = 0.0;
+        __syncthreads();
+        for (int i = 0; i < CB; ++i) {
+          double part = 0.0;
+          if (c < nb && i < nb && i >= c)
+            for (int k = c + s; k < i; k += 8) part = fma(T0[i][k], T1[k][c], part);
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          part += __shfl_xor_sync(0xffffffffu, part, 4);
+          if (s == 0 && c < nb && i < nb && i >= c) T1[i][c] = ((i == c ? 1.0 : 0.0) - part) * rdiag[i];
+          __syncthreads();
+        }
+        tile_store(T0, L, n, K, K);
+        double* dk = di + (size_t)K * CB * CB;
+        for (int e = tid; e < CB * CB; e += blockDim.x) __stcg(dk + e, T1[e / CB][e % CB]);
+      }
+    }
+    grid.sync();
+    if (*(volatile int*)bad) return;
+    // ---- panel: L_IK = A_IK DI_K^T, I > K
+    const double* dk = di + (size_t)K * CB * CB;
+    for (int I = K + 1 + r; I < nt; I += P) {
+      for (int e = tid; e < CB * CB; e += blockDim.x) T1[e / CB][e % CB] = __ldcg(dk + e);
+      tile_load(T0, L, n, I, K);
+      for (int e = tid; e < CB * CB; e += blockDim.x) T2[e / CB][e % CB] = 0.0;
+      __syncthreads();
+      tile_acc(T2, T0, T1, true, 1.0);
+      __syncthreads();
+      tile_store(T2, L, n, I, K);
+      __syncthreads();
+    }
+    grid.sync();
+    // ---- trailing update of the lower triangle: A_IJ -= L_IK L_JK^T, K < J <= I
+    {
+      const int m = nt - K - 1;
+      const int tiles = m * (m + 1) / 2;
+      for (int t = r; t < tiles; t += P) {
+        // t -> (I, J) with J <= I: row a = I - K - 1 holds a + 1 tiles
+        int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while ((a + 1) * (a + 2) / 2 <= t) ++a;
+        while (a * (a + 1) / 2 > t) --a;
+        const int I = K + 1 + a, J = K + 1 + (t - a * (a + 1) / 2);
+        tile_load(T0, L, n, I, K);
+        tile_load(T1, L, n, J, K);
+        tile_load(T2, L, n, I, J);
+        __syncthreads();
+        tile_acc(T2, T0, T1, true, -1.0);
+        __syncthreads();
+        tile_store(T2, L, n, I, J);
+        __syncthreads();
+      }
+    }
+    grid.sync();
+  }
+  // L^-1: B = I in Linv; per block row K: X_K,: = DI_K B_K,: (column tiles <= K), then
+  // B_I,: -= L_IK X_K,: for I > K
+  for (int K = 0; K < nt; ++K) {
+    const double* dk = di + (size_t)K * CB * CB;
+    for (int J = r; J <= K; J += P) {
+      for (int e = tid; e < CB * CB; e += blockDim.x) T1[e / CB][e % CB] = __ldcg(dk + e);
+      tile_load(T0, Linv, n, K, J);
+      for (int e = tid; e < CB * CB; e += blockDim.x) T2[e / CB][e % CB] = 0.0;
+      __syncthreads();
+      tile_acc(T2, T1, T0, false, 1.0);
+      __syncthreads();
+      tile_store(T2, Linv, n, K, J);
+      __syncthreads();
+    }
+    grid.sync();
+    const int rows = nt - K - 1, tiles = rows * (K + 1);
+    for (int t = r; t < tiles; t += P) {
+      const int I = K + 1 + t / (K + 1), J = t % (K + 1);
+      tile_load(T0, L, n, I, K);
+      tile_load(T1, Linv, n, K, J);
+      tile_load(T2, Linv, n, I, J);
+      __syncthreads();
+      tile_acc(T2, T0, T1, false, -1.0);
+      __syncthreads();
+      tile_store(T2, Linv, n, I, J);
+      __syncthreads();
+    }
+    grid.sync();
+  }
+  if (r == 0 && tid == 0) *info = 0;
+}
+
 // ------------------------------------------------------------------ Householder tridiagonalisation
 // M (n x n, column-major, full symmetric storage, destroyed).  Outputs: d (n), e (n-1), the
 // Householder vectors H(:, k) = v_k (rows k+1 .. n-1, v_k(k+1) = 1) and tau (n-1), so that
@@ -1163,6 +1342,24 @@ void launch_backtransform(cudaStream_t s, int n, const double* H, const double* 
 int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Linv, int* d_info, int num_sms,
                          DevBuf<double>& scratch) {
   RC_CHECK(n >= 1 && n <= 6144, RCHFSI_ERR_UNSUPPORTED, "cholesky_inverse: order out of [1, 6144]");
+  // blocked on a cooperative grid (5 grid barriers per 32 columns, FP64 work on every SM)
+  {
+    const int nt = (n + CB - 1) / CB;
+    const size_t need = (size_t)nt * CB * CB + 8;
+    double* di = scratch.ensure(std::max(need, 3 * (size_t)n));
+    int* bad = reinterpret_cast<int*>(di + (size_t)nt * CB * CB);
+    int per_sm = 0;
+    RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_blocked_kernel, 256, 0));
+    if (per_sm >= 1) {
+      const int P = std::max(1, std::min(num_sms, nt * (nt + 1) / 2));
+      const double* Ac = A;
+      void* argv[] = {(void*)&n, (void*)&Ac, (void*)&L, (void*)&Linv, (void*)&di, (void*)&bad, (void*)&d_info};
+      RC_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chol_inv_blocked_kernel), dim3(P), dim3(256),
+                                          argv, 0, s));
+      RC_LAUNCH();
+      return 0;
+    }
+  }
   double* xch = scratch.ensure(3 * (size_t)n);
   double* dinv = xch + 2 * (size_t)n;
   if (n <= 4096 && launch_resident(s, chol_inv_smem_kernel<true>, chol_inv_smem_kernel<false>, n, num_sms, n,
