@@ -278,7 +278,7 @@ def psweep_run(args, torch, dev):
     dA, dB, dD, X0 = T(c["A"]), T(c["B"]), T(c["Dinv"]), T(prob["X0"])
     out = []
     for prec in ("tf32", "bf16", "fp32"):
-        for p in (10, 20, 30, 40, 60, 80, 120):
+        for p in (10, 20, 30, 40, 60, 80, 100, 120):
             s = Solver(prob["m"], nev=prob["nev"], block=prob["block"], degree=p, precision=prec, max_iter=300,
                        tol=prob["tol"], rr_mode=args.rr, eig_mode=args.eig)
             s.set_dense(dA, B=dB, Dinv=dD)
@@ -289,7 +289,8 @@ def psweep_run(args, torch, dev):
             torch.cuda.synchronize()
             out.append({"precision": prec, "degree": p, "ms": round((time.perf_counter() - t0) * 1e3, 1),
                         "iterations": st["iterations"], "status": st["status"],
-                        "max_rel_residual": st["max_rel_residual"], "t_filter_ms": round(st["t_filter_ms"], 1)})
+                        "max_rel_residual": st["max_rel_residual"], "t_filter_ms": round(st["t_filter_ms"], 1),
+                        "cholqr_retries": st.get("cholqr_retries")})
             s.close()
     return out
 
