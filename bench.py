@@ -858,21 +858,24 @@ def end_to_end(prob, args, torch):
         h2d = sum(a.nbytes for a in ops)
         setop = lambda: s.set_fe(*ops)  # noqa: E731
     X0 = pinned(prob["X0"])
+    Xw = pinned(prob["X0"])  # the in/out block of rchfsi_solve, refilled before every step
     h2d += X0.nbytes
     d2h = X0.nbytes + 2 * N * 8
     setop()
-    s.solve(X0)
+    s.solve(Xw, inplace=True)
     ts = []
     for _ in range(max(1, min(args.steps, 3))):
+        np.copyto(Xw, X0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         setop()
-        X, ev, res, st = s.solve(X0)
+        X, ev, res, st = s.solve(Xw, inplace=True)
         torch.cuda.synchronize()
         ts.append((time.perf_counter() - t0) * 1e3)
     s.close()
     return {"value": round(statistics.mean(ts), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "includes": "rchfsi_set_operator + rchfsi_solve from host buffers"}
+            "d2h_bytes_per_step": int(d2h),
+            "includes": "rchfsi_set_operator + rchfsi_solve from pinned host buffers (X0 in, Ritz vectors out)"}
 
 
 def cpu_baseline(prob, gpu_iters):

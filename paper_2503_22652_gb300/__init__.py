@@ -219,9 +219,14 @@ class Solver:
                     self.h)
         return lmax.value, nA.value
 
-    def solve(self, X0, allow_not_converged=False):
-        """Algorithm 1 (rchfsi_solve).  Returns (X, evals, rel_resid, stats_dict)."""
-        X = X0.copy() if isinstance(X0, np.ndarray) else X0.clone()
+    def solve(self, X0, allow_not_converged=False, inplace=False):
+        """Algorithm 1 (rchfsi_solve).  Returns (X, evals, rel_resid, stats_dict).  With inplace=True
+        X0 itself (C-contiguous float64 host array, e.g. pinned memory, or a CUDA tensor) is the
+        rchfsi_solve in/out block and receives the Ritz vectors; otherwise a copy is."""
+        if inplace:
+            X = X0
+        else:
+            X = X0.copy() if isinstance(X0, np.ndarray) else X0.clone()
         X = _check_arr(X, (self.m, self.N), "X0", self.dt)
         ev = np.empty(self.N)
         res = np.empty(self.N)

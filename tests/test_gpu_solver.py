@@ -125,3 +125,17 @@ def test_chfsi_stagnates_where_rchfsi_converges():
         out[meth] = st["max_abs_residual"]
     assert out["chfsi"] > 1e-5
     assert out["rchfsi"] < 1e-11
+
+
+def test_solve_inplace_block_matches_copy():
+    """solve(..., inplace=True) uses the caller's host array as the rchfsi_solve in/out block: the
+    same Ritz pairs as the copying call, written into that array."""
+    case = dense_case(m=300, N=24, generalized=True)
+    s = make_solver(case, 24, precision="tf32", tol=1e-8, max_iter=200)
+    X_ref, ev_ref, _, st_ref = s.solve(case["X"])
+    Xw = np.ascontiguousarray(case["X"].copy())
+    X, ev, _, st = s.solve(Xw, inplace=True)
+    assert X is Xw
+    assert st["iterations"] == st_ref["iterations"]
+    np.testing.assert_allclose(ev, ev_ref, rtol=1e-12, atol=1e-12 * np.abs(ev_ref).max())
+    assert relfro(Xw, X_ref) <= 1e-10
