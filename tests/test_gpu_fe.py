@@ -130,3 +130,19 @@ def test_fe_fp64_products_tensor_core_complex():
     s.set_fe(q["cell_dofs"], q["A_cells"], q["B_cell"], q["Dinv"])
     Wg, _ = s.residual(X, L)
     assert relfro(Wg, W) <= 1e-13
+
+
+def test_fe_fp64_products_mark_nonfinite_columns(fe3):
+    """The FP64-accurate products sum in fixed point on per-column scales: a NaN in one column of X
+    makes that column of the residual NaN and leaves the other columns exact."""
+    p, A, B = fe3
+    N = 70
+    X, L, W = _inputs(p, A, B, N, seed=3)
+    Xb = X.copy()
+    Xb[17, 5] = np.nan
+    s = _solver(p, N, rr_mode="emulated")
+    Wg, _ = s.residual(Xb, L)
+    assert np.all(np.isnan(Wg[:, 5]))
+    keep = np.arange(N) != 5
+    assert np.all(np.isfinite(Wg[:, keep]))
+    assert relfro(Wg[:, keep], W[:, keep]) <= 1e-13
