@@ -83,28 +83,40 @@ __device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t smem_addr) {
 }
 
 // Pack cell matrices (n_cells x nc x nc FP64 row-major) into per-cell images of the 7 BF16 slices,
-// [cell][s][128 x 128 K-major swizzled], and the per-row exponents [cell][128].
-__global__ void pack_slices_kernel(int64_t n_cells, int nc, const double* __restrict__ A, uint8_t* __restrict__ img,
-                                   int* __restrict__ rexp) {
+// [cell][s][128 x 128 K-major swizzled], and the per-row exponents [cell][128]: first the row
+// exponents, one warp per padded row (-100000 for a zero or padding row: it adds nothing, so it
+// sets no scale), then the digits, one thread per (row, k) element.
+__global__ void slice_rowexp_kernel(int64_t n_cells, int nc, const double* __restrict__ A, int* __restrict__ rexp) {
   const int64_t rows = n_cells * kNCP;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows; e += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < rows;
+       e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t c = e / kNCP;
     const int r = (int)(e % kNCP);
-    const double* row = A + (c * nc + r) * nc;
     int ea = -100000;
-    if (r < nc)
-      for (int k = 0; k < nc; ++k) ea = max(ea, exp_of(row[k]));
-    rexp[e] = ea;  // -100000 for a zero row (it adds nothing, so it sets no scale)
-    if (ea == -100000) ea = 0;
-    uint8_t* base = img + c * (int64_t)S * kASlice;
-    for (int k = 0; k < kNCP; ++k) {
-      long long f = (r < nc && k < nc) ? fixed56(row[k], ea) : 0;
-      for (int s = 0; s < S; ++s) {
-        const int t = (int)next_digit(f, s);
-        *reinterpret_cast<__nv_bfloat16*>(base + (size_t)s * kASlice + sw_off2(r, k, kNCP)) =
-            __float2bfloat16_rn((float)t);
-      }
+    if (r < nc) {
+      const double* row = A + (c * nc + r) * nc;
+      for (int k = lane; k < nc; k += 32) ea = max(ea, exp_of(row[k]));
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+    if (lane == 0) rexp[e] = ea;
+  }
+}
+
+__global__ void pack_slices_kernel(int64_t n_cells, int nc, const double* __restrict__ A, const int* __restrict__ rexp,
+                                   uint8_t* __restrict__ img) {
+  const int64_t total = n_cells * kNCP * kNCP;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / (kNCP * kNCP);
+    const int r = (int)((e / kNCP) % kNCP), k = (int)(e % kNCP);
+    int ea = rexp[c * kNCP + r];
+    if (ea == -100000) ea = 0;
+    long long f = (r < nc && k < nc) ? fixed56(A[(c * nc + r) * nc + k], ea) : 0;
+    uint8_t* base = img + c * (int64_t)S * kASlice + sw_off2(r, k, kNCP);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      *reinterpret_cast<__nv_bfloat16*>(base + (size_t)s * kASlice) = __float2bfloat16_rn((float)(int)next_digit(f, s));
   }
 }
 
@@ -573,10 +585,13 @@ void ensure_slices(cudaStream_t s, const FeOp& op, bool useB) {
   img.ensure((size_t)cells * S * kASlice);
   ex.ensure((size_t)cells * kNCP);
   const double* src = useB ? op.B64.p : op.A64.p;
-  RC_CUDA(cudaMemsetAsync(img.p, 0, (size_t)cells * S * kASlice, s));
   const int64_t rows = cells * kNCP;
-  pack_slices_kernel<<<(unsigned)std::min<int64_t>((rows + 127) / 128, 152 * 8), 128, 0, s>>>(cells, op.nc, src,
-                                                                                            img.p, ex.p);
+  slice_rowexp_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, 152 * 32)), 256, 0,
+                        s>>>(cells, op.nc, src, ex.p);
+  RC_LAUNCH();
+  const int64_t total = rows * kNCP;
+  pack_slices_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32)), 256, 0,
+                       s>>>(cells, op.nc, src, ex.p, img.p);
   RC_LAUNCH();
 }
 
