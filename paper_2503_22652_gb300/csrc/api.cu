@@ -917,7 +917,8 @@ int rayleigh_ritz(rchfsi_ctx& c, double* Y, double* X, double* AX, double* BX, d
     } else if (c.p.eig_mode == RCHFSI_EIG_TRIDIAG) {
       // keep a copy of M for the library fallback (a cluster of close eigenvalues too large)
       RC_CUDA(cudaMemcpyAsync(w.Lb.p, w.Z.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));
-      if (sym_eig_f64(c.s, N, w.Z.p, w.Zt.p, evals, w.eigws, w.info.p + 3, c.num_sms)) {
+      const OzScratch oz{&w.ozR, &w.ozE, &w.ozws, eflag, c.num_sms};
+      if (sym_eig_f64(c.s, N, w.Z.p, w.Zt.p, evals, w.eigws, w.info.p + 3, c.num_sms, emu ? &oz : nullptr)) {
         vec = w.Zt.p;
       } else {
         RC_CUDA(cudaMemcpyAsync(w.Z.p, w.Lb.p, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, c.s));

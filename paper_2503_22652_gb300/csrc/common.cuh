@@ -172,8 +172,11 @@ int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Li
 // Symmetric eigensolver (small_eig.cu: Householder tridiagonalisation, bisection, inverse iteration):
 // M destroyed; V (column-major eigenvectors) and evals ascending.  Returns false when it declines the
 // problem (order > 3072 or a cluster of close eigenvalues too large for inverse iteration).
+// oz: when set, the N x N products of its orthogonalisation step run FP64-accurate on the tensor
+// cores (oz_gemm.cuh) instead of as FP64 GEMMs.
+struct OzScratch;
 bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, int* d_flag,
-                 int num_sms);
+                 int num_sms, const OzScratch* oz = nullptr);
 // Symmetric eigensolver (parallel cyclic Jacobi, jacobi.cu): M destroyed; V, evals ascending.
 int jacobi_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, double tol,
                    int max_sweeps);

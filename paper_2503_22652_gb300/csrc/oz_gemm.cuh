@@ -40,4 +40,13 @@ void oz_slice(cudaStream_t s, int64_t R, int64_t K, const double* X, int64_t rs,
 void oz_gemm(cudaStream_t s, int num_sms, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc,
              DevBuf<double>& ws, int* err, bool symmetric = false);
 
+// Operand and workspace buffers lent to a caller's FP64-accurate products (the eigensolver).
+struct OzScratch {
+  OzOperand* a;
+  OzOperand* b;
+  DevBuf<double>* ws;
+  int* err;
+  int num_sms;
+};
+
 }  // namespace rchfsi

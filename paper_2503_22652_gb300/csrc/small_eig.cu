@@ -28,6 +28,7 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "oz_gemm.cuh"
 #include "prof.cuh"
 
 namespace cg = cooperative_groups;
@@ -1182,6 +1183,15 @@ __global__ void __launch_bounds__(64) backtransform_kernel(int n, const double* 
 }
 
 // C = val * I (n x n, column-major)
+// S = 1.5 I - 0.5 S (n x n): the Newton-Schulz factor from the Gram matrix Z^T Z.
+__global__ void ns_shift_kernel(int n, double* S) {
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / n, i = t - j * n;
+    S[t] = fma(-0.5, S[t], i == j ? 1.5 : 0.0);
+  }
+}
+
 __global__ void diag_fill_kernel(int n, double* C, double val) {
   const int64_t tot = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
@@ -1370,7 +1380,7 @@ int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Li
 }
 
 bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, DevBuf<double>& ws, int* d_flag,
-                 int num_sms) {
+                 int num_sms, const OzScratch* oz) {
   if (n < 1 || n > 3072) return false;
   // workspace: H, S, V2 (n^2 each), d, e, tau, p (n each), xch (n + 8), tnorm
   const size_t nn = (size_t)n * n;
@@ -1411,6 +1421,16 @@ bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, Dev
   RC_CUDA(cudaStreamSynchronize(s));
   if (flag) return false;
   // 4. one Newton-Schulz step towards the orthogonal factor: Z <- Z (3 I - Z^T Z) / 2
+  if (oz) {
+    // FP64-accurate products from BF16 slices: G = Z^T Z (symmetric), S = 1.5 I - 0.5 G, V = Z S
+    oz_slice(s, n, n, V2, n, 1, *oz->a);  // row i = column i of Z
+    oz_gemm(s, oz->num_sms, *oz->a, *oz->a, S, n, *oz->ws, oz->err, true);
+    ns_shift_kernel<<<cdiv((int64_t)n * n, 256) < 1216 ? cdiv((int64_t)n * n, 256) : 1216, 256, 0, s>>>(n, S);
+    RC_LAUNCH();
+    oz_slice(s, n, n, V2, 1, n, *oz->b);  // row i of Z
+    oz_slice(s, n, n, S, n, 1, *oz->a);   // column j of S as row j
+    oz_gemm(s, oz->num_sms, *oz->b, *oz->a, V, n, *oz->ws, oz->err);
+  } else {
   diag_fill_kernel<<<cdiv((int64_t)n * n, 256) < 1216 ? cdiv((int64_t)n * n, 256) : 1216, 256, 0, s>>>(n, S, 1.5);
   RC_LAUNCH();
   EpiArgs g;
@@ -1427,6 +1447,7 @@ bool sym_eig_f64(cudaStream_t s, int n, double* M, double* V, double* evals, Dev
   z.ldc = n;
   z.prof_cls = RCHFSI_KERNEL_EIG;
   gemm_f64(s, n, n, n, V2, n, false, S, n, true, z);
+  }
   // 5. V = Q Z
   const int R = (n + 31) / 32;
   if (R <= 2) launch_backtransform<2>(s, n, H, tau, V);
