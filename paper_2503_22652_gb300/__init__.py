@@ -224,6 +224,9 @@ class Solver:
         X0 itself (C-contiguous float64 host array, e.g. pinned memory, or a CUDA tensor) is the
         rchfsi_solve in/out block and receives the Ritz vectors; otherwise a copy is."""
         if inplace:
+            if isinstance(X0, np.ndarray) and (X0.dtype != self.dt or not X0.flags.c_contiguous
+                                               or not X0.flags.writeable):
+                raise ValueError("inplace solve needs a writable C-contiguous %s array" % np.dtype(self.dt).name)
             X = X0
         else:
             X = X0.copy() if isinstance(X0, np.ndarray) else X0.clone()
