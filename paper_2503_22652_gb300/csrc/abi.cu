@@ -354,8 +354,28 @@ void set_fe(rchfsi_ctx& c, const rchfsi_operator* op) {
            "FE operator needs cell_dofs, A_cells, B_cells and Dinv");
   RC_CHECK(!op->A_filter && !op->Dinv_dense, RCHFSI_ERR_UNSUPPORTED,
            "A_filter / Dinv_dense are for dense operators");
+  // a new operator takes over the previous one's allocations: those set_fe rewrites, the per-product
+  // scratch and the packed images (repacked from the new matrices on first use); the rest is freed
+  std::unique_ptr<FeOp> old = std::move(c.fe);
   c.fe.reset(new FeOp());
   FeOp& f = *c.fe;
+  if (old) {
+    f.dofs.take(old->dofs);
+    f.A64.take(old->A64);
+    f.B64.take(old->B64);
+    f.Dinv.take(old->Dinv);
+    f.own_pos.take(old->own_pos);
+    f.imgADtf.take(old->imgADtf);
+    f.ozA.take(old->ozA);
+    f.ozB.take(old->ozB);
+    f.ozAe.take(old->ozAe);
+    f.ozBe.take(old->ozBe);
+    f.ozArow.take(old->ozArow);
+    f.ozBrow.take(old->ozBrow);
+    f.ozcexp.take(old->ozcexp);
+    f.ozplanes.take(old->ozplanes);
+    old.reset();
+  }
   const int64_t mc = c.cplx ? c.mc : c.p.m;  // dofs of the (complex) problem
   f.m = c.p.m;
   f.n_cells = op->n_cells;

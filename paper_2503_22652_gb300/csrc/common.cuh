@@ -77,6 +77,15 @@ struct DevBuf {
     return p;
   }
   size_t bytes() const { return n * sizeof(T); }
+  // Take over o's allocation (o is left empty); this buffer's own allocation is released.
+  void take(DevBuf& o) {
+    if (&o == this) return;
+    release();
+    p = o.p;
+    n = o.n;
+    o.p = nullptr;
+    o.n = 0;
+  }
 };
 
 inline bool is_device_pointer(const void* ptr) {

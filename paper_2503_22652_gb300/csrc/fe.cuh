@@ -41,6 +41,9 @@ struct FeOp {
   // planes of the input block)
   mutable DevBuf<uint8_t> ozA, ozB;
   mutable DevBuf<int> ozAe, ozBe, ozcexp, ozArow, ozBrow;
+  // packed from this operator's matrices (an allocation taken over from a previous operator is not)
+  mutable bool oz_packed[2] = {false, false}, rowexp_packed[2] = {false, false};
+  bool imgAD_packed = false;
   mutable DevBuf<__nv_bfloat16> ozplanes;
 };
 

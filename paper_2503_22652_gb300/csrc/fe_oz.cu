@@ -580,7 +580,7 @@ void fill_int(cudaStream_t s, int* p, int n, int v) {
 void ensure_slices(cudaStream_t s, const FeOp& op, bool useB) {
   DevBuf<uint8_t>& img = useB ? op.ozB : op.ozA;
   DevBuf<int>& ex = useB ? op.ozBe : op.ozAe;
-  if (img.p) return;
+  if (img.p && op.oz_packed[useB]) return;
   const int64_t cells = (useB && op.B_shared) ? 1 : op.n_cells;
   img.ensure((size_t)cells * S * kASlice);
   ex.ensure((size_t)cells * kNCP);
@@ -593,13 +593,14 @@ void ensure_slices(cudaStream_t s, const FeOp& op, bool useB) {
   pack_slices_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 32)), 256, 0,
                        s>>>(cells, op.nc, src, ex.p, img.p);
   RC_LAUNCH();
+  op.oz_packed[useB] = true;
 }
 
 // Per-dof scale exponents of the accumulator for op (and, for the A product of a complex operator,
 // its imaginary part, which adds into the same rows); made on first use.
 const int* ensure_rowexp(cudaStream_t s, const FeOp& op, bool useB) {
   DevBuf<int>& rx = useB ? op.ozBrow : op.ozArow;
-  if (rx.p) return rx.p;
+  if (rx.p && op.rowexp_packed[useB]) return rx.p;
   const int64_t nd = op.cplx ? op.mc : op.m;
   rx.ensure((size_t)nd);
   fill_int(s, rx.p, (int)nd, -100000);
@@ -616,6 +617,7 @@ const int* ensure_rowexp(cudaStream_t s, const FeOp& op, bool useB) {
     ensure_slices(s, *op.imag, false);
     add(*op.imag);
   }
+  op.rowexp_packed[useB] = true;
   return rx.p;
 }
 

@@ -493,11 +493,12 @@ Plan make_plan(int BN) {
 }
 
 const uint8_t* scaled_images(cudaStream_t s, FeOp& op, const double* dinv) {
-  if (!op.imgADtf.p) {
+  if (!op.imgADtf.p || !op.imgAD_packed) {
     op.imgADtf.ensure((size_t)kABytes * op.n_cells);
     const int64_t total = op.n_cells * (int64_t)kNCP * kNCP;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
     pack_scaled_kernel<<<blocks, 256, 0, s>>>(op.n_cells, op.nc, op.A64.p, op.dofs.p, dinv, op.imgADtf.p);
+    op.imgAD_packed = true;
     RC_LAUNCH();
   }
   return op.imgADtf.p;

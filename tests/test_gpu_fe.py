@@ -146,3 +146,28 @@ def test_fe_fp64_products_mark_nonfinite_columns(fe3):
     keep = np.arange(N) != 5
     assert np.all(np.isfinite(Wg[:, keep]))
     assert relfro(Wg[:, keep], W[:, keep]) <= 1e-13
+
+
+def test_fe_operator_replaced_on_the_same_handle(fe3):
+    """rchfsi_set_operator on a handle that already holds an FE operator reuses its allocations but
+    repacks every cell image: the products and the filter follow the new cell matrices."""
+    p, A, B = fe3
+    N = 40
+    X, L, _ = _inputs(p, A, B, N, seed=6)
+    s = Solver(p["m"], nev=N // 2, block=N, precision="tf32", rr_mode="emulated")
+    s.set_fe(p["cell_dofs"], p["A_cells"], p["B_cell"], p["Dinv"])
+    s.residual(X, L)
+    d = p["Dinv"]
+    s.filter(X, L, A @ X - (B @ X) * L[None, :], -25.0, 40.0, 2500.0, 6)
+    # a second operator: the cell matrices scaled and shifted by the cell mass
+    A2_cells = 1.7 * p["A_cells"] + 0.3 * p["B_cell"][None, :, :]
+    A2 = ofe.assemble(p["cell_dofs"], A2_cells, p["m"])
+    s.set_fe(p["cell_dofs"], A2_cells, p["B_cell"], p["Dinv"])
+    W2 = A2 @ X - (B @ X) * L[None, :]
+    Wg, _ = s.residual(X, L)
+    assert relfro(Wg, W2) <= 1e-13
+    ref = filters.rchfsi_filter(lambda R: A2 @ (d[:, None] * R), lambda R: d[:, None] * R, X, L, W2,
+                                -25.0, 40.0, 2500.0, 6)
+    base = X * filters.lambda_p(L, -25.0, 40.0, 2500.0, 6)[None, :]
+    got = s.filter(X, L, W2, -25.0, 40.0, 2500.0, 6)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref - base) <= 5e-3
