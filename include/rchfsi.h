@@ -114,7 +114,8 @@ typedef enum {
 
 typedef enum {
   RCHFSI_RR_FP64 = 0,          /* FP64 FMA (DFMA) GEMMs */
-  RCHFSI_RR_FP64_EMULATED = 1  /* error-free BF16 splitting, 7 slices, exact per-chunk FP32 sums */
+  RCHFSI_RR_FP64_EMULATED = 1  /* error-free BF16 splitting, 7 slices, exact per-chunk FP32 sums; the
+                                  FE cell contributions summed in 64-bit fixed point (order-free) */
 } rchfsi_rr_mode;
 
 /* Operator description for rchfsi_set_operator.  Unused fields must be 0 / NULL.
@@ -303,12 +304,13 @@ typedef enum {
   RCHFSI_KERNEL_FE_CELL_F64 = 5,   /* FE cell-matrix product of the residual / Rayleigh-Ritz (FP64) */
   RCHFSI_KERNEL_GEMM_F64_EMU = 6,  /* FP64-accurate GEMM from BF16 slices on the tensor cores; flops are
                                       the tensor-core flops (28 slice products) */
-  RCHFSI_KERNEL_SMALL_DENSE = 7,   /* N x N steps of Rayleigh-Ritz: Cholesky, triangular solves,
-                                      symmetrisation */
+  RCHFSI_KERNEL_SMALL_DENSE = 7,   /* N x N steps of Rayleigh-Ritz: Cholesky and L^-1, the N x N
+                                      FP64 GEMMs of rr_mode fp64, symmetrisation */
   RCHFSI_KERNEL_EIG = 8,           /* projected N x N eigensolver (this library's tridiagonal or Jacobi
                                       kernels, or the cuSOLVER dsyevd call of RCHFSI_EIG_SYEVD) */
   RCHFSI_KERNEL_RR_AUX = 9,        /* m x N passes of Rayleigh-Ritz: column norms and scaling, BF16
-                                      slicing of the emulated GEMM operands */
+                                      slicing of the emulated GEMM and FE product operands, and the
+                                      FE products' fixed-point to FP64 conversion */
   RCHFSI_KERNEL_CLASSES = 10
 } rchfsi_kernel_class;
 
