@@ -294,20 +294,20 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(int n, const double*
 // first column j whose pivot is not positive (L and L^-1 are then not written in full).
 constexpr int CB = 32;
 
-// C(32 x 32 tile in shared memory, row-major stride 33) (+|-)= A B^T or A B, the tiles staged in
-// shared memory; 256 threads, 4 outputs each (rows ty + 8 u, column tx).
-__device__ __forceinline__ void tile_acc(double (*C)[CB + 1], const double (*A)[CB + 1], const double (*B)[CB + 1],
-                                         bool btrans, double sign) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+// Rows [r0, r0 + nr) x columns [c0, c0 + nc) of C (+|-)= A B^T or A B, the tiles staged in shared
+// memory; 256 threads over the part's outputs.
+__device__ __forceinline__ void tile_acc_part(double (*C)[CB + 1], const double (*A)[CB + 1], const double (*B)[CB + 1],
+                                              bool btrans, double sign, int r0, int nr, int c0, int nc) {
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int r = r0 + e / nc, c = c0 + e % nc;
+    double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
-  for (int k = 0; k < CB; ++k) {
-    const double b = btrans ? B[tx][k] : B[k][tx];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = fma(A[ty + 8 * u][k], b, acc[u]);
+    for (int k = 0; k < CB; k += 2) {
+      a0 = fma(A[r][k], btrans ? B[c][k] : B[k][c], a0);
+      a1 = fma(A[r][k + 1], btrans ? B[c][k + 1] : B[k + 1][c], a1);
+    }
+    C[r][c] = fma(sign, a0 + a1, C[r][c]);
   }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) C[ty + 8 * u][tx] = fma(sign, acc[u], C[ty + 8 * u][tx]);
 }
 
 // Tile (I, J) of a column-major n x n matrix to / from shared memory (zeros outside the matrix).
@@ -320,6 +320,13 @@ __device__ __forceinline__ void tile_load(double (*T)[CB + 1], const double* M, 
 __device__ __forceinline__ void tile_store(const double (*T)[CB + 1], double* M, int n, int I, int J) {
   for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
     const int c = e / CB, r = e % CB, i = I * CB + r, j = J * CB + c;
+    if (i < n && j < n) __stcg(M + (size_t)j * n + i, T[r][c]);
+  }
+}
+__device__ __forceinline__ void tile_store_part(const double (*T)[CB + 1], double* M, int n, int I, int J, int r0,
+                                                int nr, int c0, int nc) {
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int c = c0 + e / nr, r = r0 + e % nr, i = I * CB + r, j = J * CB + c;
     if (i < n && j < n) __stcg(M + (size_t)j * n + i, T[r][c]);
   }
 }
@@ -397,14 +404,16 @@ __global__ void __launch_bounds__(256) chol_inv_blocked_kernel(int n, const doub
     if (*(volatile int*)bad) return;
     // ---- panel: L_IK = A_IK DI_K^T, I > K
     const double* dk = di + (size_t)K * CB * CB;
-    for (int I = K + 1 + r; I < nt; I += P) {
+    // (two CTAs per tile, one per half of its rows: a row of L_IK needs only that row of A_IK)
+    for (int t = r; t < 2 * (nt - K - 1); t += P) {
+      const int I = K + 1 + t / 2, h = (t % 2) * (CB / 2);
       for (int e = tid; e < CB * CB; e += blockDim.x) T1[e / CB][e % CB] = __ldcg(dk + e);
       tile_load(T0, L, n, I, K);
       for (int e = tid; e < CB * CB; e += blockDim.x) T2[e / CB][e % CB] = 0.0;
       __syncthreads();
-      tile_acc(T2, T0, T1, true, 1.0);
+      tile_acc_part(T2, T0, T1, true, 1.0, h, CB / 2, 0, CB);
       __syncthreads();
-      tile_store(T2, L, n, I, K);
+      tile_store_part(T2, L, n, I, K, h, CB / 2, 0, CB);
       __syncthreads();
     }
     grid.sync();
@@ -412,7 +421,9 @@ __global__ void __launch_bounds__(256) chol_inv_blocked_kernel(int n, const doub
     {
       const int m = nt - K - 1;
       const int tiles = m * (m + 1) / 2;
-      for (int t = r; t < tiles; t += P) {
+      // (four CTAs per tile, one per quadrant of outputs; the operands are other tiles)
+      for (int tq = r; tq < 4 * tiles; tq += P) {
+        const int t = tq / 4, qr = ((tq % 4) / 2) * (CB / 2), qc = (tq % 2) * (CB / 2);
         // t -> (I, J) with J <= I: row a = I - K - 1 holds a + 1 tiles
         int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
         while ((a + 1) * (a + 2) / 2 <= t) ++a;
@@ -422,9 +433,9 @@ __global__ void __launch_bounds__(256) chol_inv_blocked_kernel(int n, const doub
         tile_load(T1, L, n, J, K);
         tile_load(T2, L, n, I, J);
         __syncthreads();
-        tile_acc(T2, T0, T1, true, -1.0);
+        tile_acc_part(T2, T0, T1, true, -1.0, qr, CB / 2, qc, CB / 2);
         __syncthreads();
-        tile_store(T2, L, n, I, J);
+        tile_store_part(T2, L, n, I, J, qr, CB / 2, qc, CB / 2);
         __syncthreads();
       }
     }
@@ -434,27 +445,30 @@ __global__ void __launch_bounds__(256) chol_inv_blocked_kernel(int n, const doub
   // B_I,: -= L_IK X_K,: for I > K
   for (int K = 0; K < nt; ++K) {
     const double* dk = di + (size_t)K * CB * CB;
-    for (int J = r; J <= K; J += P) {
+    // (two CTAs per tile, one per half of its columns: a column of X_KJ needs only that column of B_KJ)
+    for (int t = r; t < 2 * (K + 1); t += P) {
+      const int J = t / 2, h = (t % 2) * (CB / 2);
       for (int e = tid; e < CB * CB; e += blockDim.x) T1[e / CB][e % CB] = __ldcg(dk + e);
       tile_load(T0, Linv, n, K, J);
       for (int e = tid; e < CB * CB; e += blockDim.x) T2[e / CB][e % CB] = 0.0;
       __syncthreads();
-      tile_acc(T2, T1, T0, false, 1.0);
+      tile_acc_part(T2, T1, T0, false, 1.0, 0, CB, h, CB / 2);
       __syncthreads();
-      tile_store(T2, Linv, n, K, J);
+      tile_store_part(T2, Linv, n, K, J, 0, CB, h, CB / 2);
       __syncthreads();
     }
     grid.sync();
     const int rows = nt - K - 1, tiles = rows * (K + 1);
-    for (int t = r; t < tiles; t += P) {
+    for (int tq = r; tq < 4 * tiles; tq += P) {
+      const int t = tq / 4, qr = ((tq % 4) / 2) * (CB / 2), qc = (tq % 2) * (CB / 2);
       const int I = K + 1 + t / (K + 1), J = t % (K + 1);
       tile_load(T0, L, n, I, K);
       tile_load(T1, Linv, n, K, J);
       tile_load(T2, Linv, n, I, J);
       __syncthreads();
-      tile_acc(T2, T0, T1, false, -1.0);
+      tile_acc_part(T2, T0, T1, false, -1.0, qr, CB / 2, qc, CB / 2);
       __syncthreads();
-      tile_store(T2, Linv, n, I, J);
+      tile_store_part(T2, Linv, n, I, J, qr, CB / 2, qc, CB / 2);
       __syncthreads();
     }
     grid.sync();
@@ -1361,7 +1375,7 @@ int cholesky_inverse_f64(cudaStream_t s, int n, double* A, double* L, double* Li
     int per_sm = 0;
     RC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_blocked_kernel, 256, 0));
     if (per_sm >= 1) {
-      const int P = std::max(1, std::min(num_sms, nt * (nt + 1) / 2));
+      const int P = std::max(1, std::min(num_sms, 2 * nt * (nt + 1)));
       const double* Ac = A;
       void* argv[] = {(void*)&n, (void*)&Ac, (void*)&L, (void*)&Linv, (void*)&di, (void*)&bad, (void*)&d_info};
       RC_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chol_inv_blocked_kernel), dim3(P), dim3(256),
