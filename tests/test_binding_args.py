@@ -33,3 +33,17 @@ def test_torch_blocks_checked_not_copied():
         _check_arr(t, (3, 4), "X", np.complex128)           # real tensor for a complex block
     z = torch.ones(3, 4, dtype=torch.complex128)
     assert _check_arr(z, (3, 4), "X", np.complex128) is z
+
+
+def test_inplace_solve_refuses_arrays_it_would_copy():
+    """solve(inplace=True) writes the Ritz vectors into the caller's array, so an array the binding
+    would have to convert or copy (wrong dtype, not C-contiguous, read-only) is refused before any
+    library call."""
+    from paper_2503_22652_gb300 import Solver
+    s = object.__new__(Solver)  # no handle: the check comes before the library is touched
+    s.dt, s.m, s.N = np.float64, 3, 4
+    ro = np.ones((3, 4))
+    ro.flags.writeable = False
+    for bad in (np.ones((3, 4), dtype=np.float32), np.asfortranarray(np.ones((3, 4))), ro):
+        with pytest.raises(ValueError):
+            s.solve(bad, inplace=True)
